@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: coarsest-level solves/s at relative residual 1e-10 on the Wilson-clover
+8^4 coarse lattice (n = 32 dof per site, 131072 unknowns), with the D_c apply's
+achieved HBM bandwidth against the measured peak.
+
+One step = one right-hand side solved to a true FP64 relative residual of
+1e-10 with GMRES(50) + Leja-ordered degree-4 polynomial + GCRO-DR k = 16
+(u = 10) in the inner precision, inside FP64 iterative refinement.  The
+polynomial and the recycle space are built during the warm-up solves and
+reused, as for repeated coarsest-level solves with one operator.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FINE_DIMS = (16, 16, 16, 16)
+NV = 16
+M0 = -0.42
+CSW = 1.0
+KEY = (2, 0)
+PARAMS = dict(m=50, poly_degree=4, defl_k=16, recycle_updates=10, tol=1e-10, max_restarts=100, max_ir=20)
+WORKLOAD = ("wilson-clover coarse 8^4 (fine 16^4, 2^4 aggregates), nv=16 -> n=32, 131072 unknowns, "
+            "m0=-0.42, c_sw=1.0; GMRES(50) + Leja poly d=4 + GCRO-DR k=16 u=10; {prec} inner + FP64 "
+            "refinement to 1e-10")
+ORACLE_ITERS = os.path.join(ROOT, "oracle", "bench_workload_iterations.json")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_gb300(args):
+    import torch
+
+    import paper_2205_09104_gb300 as cg
+    from synthetic import draws
+    from synthetic.coarse_op import build_coarse_operator
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = cg.PREC_BF16 if args.prec == "bf16" else cg.PREC_FP32
+    # replicas: each rank solves its own right-hand sides with its own copy of the operator
+    op = build_coarse_operator(KEY, FINE_DIMS, NV, M0, CSW, device=dev)
+    cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(prec,))
+    del op
+    torch.cuda.empty_cache()
+    n, V = 2 * NV, cop.V
+    N = V * n
+    total = args.warmup + 2 * args.steps
+    B = torch.from_numpy(draws.rhs((*KEY, 100 + rank), total, N)).to(dev)
+    X = torch.zeros_like(B)
+    inner_tol = 1e-5 if prec == cg.PREC_FP32 else 1e-2
+    p = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS, **PARAMS)
+    pt = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS | cg.COARSE_TIME_APPLY,
+                         **PARAMS)
+    for i in range(args.warmup):
+        cop.solve(B[i], X[i], params=p)
+    torch.cuda.synchronize()
+    barrier = (lambda: __import__("torch.distributed").distributed.barrier()) if world > 1 else (lambda: None)
+    infos = []
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(args.steps):
+            _, inf = cop.solve(B[args.warmup + i], X[args.warmup + i], params=pt)
+            infos.append(inf[0])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+    worst_res = max(i["rel_residual"] for i in infos)
+    # end to end: pinned host b -> device, solve, device x -> pinned host, every step
+    hb = B[args.warmup + args.steps:].cpu().pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    db = torch.empty(N, dtype=torch.complex128, device=dev)
+    dx = torch.empty_like(db)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.steps):
+        db.copy_(hb[i], non_blocking=True)
+        cop.solve(db, dx, params=p)
+        hx[i].copy_(dx, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    # roofline of the stencil apply (the dominant kernel): algorithmic bytes per launch
+    esize = 4 if prec == cg.PREC_BF16 else 8
+    bytes_per_apply = 5 * n * n * V * esize + 2 * N * 8
+    apply_ms = sum(i["apply_ms"] for i in infos)
+    apply_cnt = sum(i["apply_count"] for i in infos)
+    avg = apply_ms / max(apply_cnt, 1)
+    achieved = bytes_per_apply / (avg * 1e-3) / 1e9
+    peak, src = peaks()
+    iters = statistics.mean(i["iterations"] for i in infos)
+    line = {
+        "metric": "coarsest-level solves/s at rel. residual 1e-10",
+        "value": round(value, 3),
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == cg.PREC_FP32 else "bf16",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.format(prec=args.prec.upper()), "l2": "inputs larger than L2 "
+                   "(FP64 blocks 335 MB read every refinement step; FP32 blocks 168 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(world * args.steps / (ms_e2e / 1e3), 3), "unit": "solves/s",
+                "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
+        "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": f"k_apply<32,{'cbf16' if esize == 4 else 'float2'}>",
+                     "bytes_per_launch": bytes_per_apply, "avg_launch_us": round(avg * 1e3, 2),
+                     "launches_timed": apply_cnt, "peak_source": src},
+        "solver": {"iterations_per_solve": iters, "matvecs_per_solve": statistics.mean(i["matvecs"] for i in infos),
+                   "ir_steps": statistics.mean(i["ir_steps"] for i in infos), "worst_rel_residual": worst_res,
+                   "recycle_updates": infos[-1]["recycle_updates"]},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cop, iters, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    cop.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def oracle_workload():
+    """Blocks of the bench operator on the host (built with the shared generator on the CPU)."""
+    from synthetic.coarse_op import build_coarse_operator
+    op = build_coarse_operator(KEY, FINE_DIMS, NV, M0, CSW, device="cpu")
+    return op
+
+
+def oracle_sample(s, h, dims, budget_s: float, steps: int):
+    """Time the oracle's FP64 GCRO-DR (GMRES(50), degree-4 polynomial, k=16) for its first
+    `steps` Arnoldi steps on one right-hand side; returns seconds per Arnoldi step."""
+    from oracle import coarse as oc
+    from oracle import krylov
+    from synthetic import draws
+    N = s.shape[0] * s.shape[1]
+    A = lambda v: oc.apply(s, h, dims, v)
+    v0 = draws.poly_start(KEY, N)
+    theta, _ = krylov.poly_setup(A, v0, PARAMS["poly_degree"])
+    M = lambda v: krylov.poly_apply(A, theta, v)
+    b = draws.rhs((*KEY, 999), 1, N)[0]
+    t0 = time.perf_counter()
+    krylov.gmres(A, b, m=steps, tol=1e-300, max_restarts=1, precond=M)
+    return (time.perf_counter() - t0) / steps
+
+
+def oracle_iterations():
+    try:
+        with open(ORACLE_ITERS) as f:
+            return json.load(f)["iterations_per_solve"], "oracle run to 1e-10 (stored)"
+    except Exception:
+        return None, None
+
+
+def cpu_baseline(cop, gpu_iters, budget_s=20.0):
+    op = oracle_workload()
+    s, h = op.self_blocks.numpy(), op.hop_blocks.numpy()
+    steps = 8
+    per_step = oracle_sample(s, h, op.dims, budget_s, steps)
+    iters, src = oracle_iterations()
+    if iters is None:
+        iters, src = gpu_iters, "Arnoldi steps per solve of this run"
+    return {"value": round(1.0 / (per_step * iters), 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle FP64 pp-GMRES, {steps} Arnoldi steps (d=4: {4 * steps} applies + MGS) on one "
+                      f"right-hand side; seconds per step x {iters:.0f} steps per solve ({src}); NumPy einsum, "
+                      f"single thread"}
+
+
+def run_reference(args):
+    world, rank, local = dist_init()
+    if rank != 0:
+        return
+    op = oracle_workload()
+    s, h = op.self_blocks.numpy(), op.hop_blocks.numpy()
+    iters, src = oracle_iterations()
+    if iters is None:
+        iters, src = 200.0, "assumed 200 Arnoldi steps per solve"
+    steps = 4
+    for _ in range(args.warmup):
+        oracle_sample(s, h, op.dims, 10, steps)
+    t = []
+    for _ in range(args.steps):
+        t.append(oracle_sample(s, h, op.dims, 10, steps))
+    per = statistics.mean(t)
+    value = 1.0 / (per * iters)
+    line = {"impl": "reference", "metric": "coarsest-level solves/s at rel. residual 1e-10", "value": round(value, 6),
+            "unit": "solves/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(per * iters * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(prec="FP64 oracle")},
+            "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {steps} Arnoldi steps of the FP64 oracle pp-GMRES; seconds per "
+                                       f"step x {iters:.0f} steps per solve ({src})"},
+            "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

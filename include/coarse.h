@@ -1,0 +1,226 @@
+/*
+ * coarse.h -- C ABI of the GB300 coarsest-level solver for aggregation-based
+ * multigrid (coarse Wilson-clover / twisted-mass Dirac stencil D_c).
+ *
+ * Paper: "Coarsest-level improvements in multigrid for lattice QCD on
+ * large-scale computers", arXiv:2205.09104.
+ *
+ * General conventions
+ *   - Every pointer named as "device" must point to memory of the current CUDA
+ *     device; every "host" pointer to host memory.  Streams are cudaStream_t
+ *     passed as void* (NULL = legacy default stream).
+ *   - Complex numbers are interleaved (re, im) pairs: complex128 = 2 x double,
+ *     complex64 = 2 x float.
+ *   - Lattice: dims[4] = (L0, L1, L2, L3), V = L0 L1 L2 L3 sites, site index
+ *     x = x0 + L0*(x1 + L1*(x2 + L2*x3)), periodic boundaries.
+ *   - n = 2*nv unknowns per site: the nv chirality-+ dofs first, then nv
+ *     chirality-- dofs; sigma3 = diag(+1 x nv, -1 x nv).
+ *   - Vectors are [nrhs][V][n] complex, contiguous.
+ *   - Return value: COARSE_OK (0) or a negative coarse_status.  No call aborts
+ *     or throws; the message of the last failure on the calling thread is
+ *     returned by coarse_last_error().
+ */
+#ifndef COARSE_H
+#define COARSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct coarse_op coarse_op; /* opaque operator handle */
+
+typedef enum {
+  COARSE_OK = 0,
+  COARSE_ERR_INVALID_ARG = -1,   /* bad pointer, size or parameter */
+  COARSE_ERR_OOM = -2,           /* device allocation failed */
+  COARSE_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  COARSE_ERR_NOT_CONVERGED = -4, /* tolerance not reached; x holds the best iterate */
+  COARSE_ERR_BREAKDOWN = -5,     /* Krylov breakdown that could not be recovered */
+  COARSE_ERR_NONFINITE = -6,     /* NaN/Inf met in the data or the iteration */
+  COARSE_ERR_TIMEOUT = -7,       /* a bounded device-side wait ran out */
+  COARSE_ERR_NOT_GAMMA5 = -8     /* blocks violate sigma3 D_c sigma3 = D_c^H */
+} coarse_status;
+
+/* Arithmetic of a coarse apply or of the inner solver. */
+typedef enum {
+  COARSE_PREC_FP64 = 0, /* FP64 blocks, complex128 vectors, FP64 accumulation */
+  COARSE_PREC_FP32 = 1, /* FP32 blocks, complex64 vectors, FP32 accumulation */
+  COARSE_PREC_BF16 = 2  /* BF16 blocks, complex64 vectors, FP32 accumulation */
+} coarse_precision;
+
+#define COARSE_ASSUME_GAMMA5 0x1u /* hop_blocks holds only the 4 forward hops */
+
+typedef struct {
+  int32_t dims[4];      /* coarse lattice extents, each >= 2 */
+  int32_t nv;           /* test vectors per chirality: n = 2*nv, nv in {8, 16, 24} */
+  double mu;            /* twisted mass: D_c gets + i*mu*sigma3 on the diagonal (0 = Wilson-clover) */
+  uint32_t flags;       /* COARSE_ASSUME_GAMMA5 or 0 */
+  int32_t max_nrhs;     /* largest nrhs later passed to coarse_apply / coarse_solve (>= 1) */
+  uint32_t precisions;  /* bit mask of (1u << coarse_precision) block copies to keep; FP64 always kept */
+} coarse_op_desc;
+
+/*
+ * coarse_op_create -- ingest the Galerkin blocks of D_c = P^H D P.
+ *
+ * Sec. 2.2 (aggregation-based AMG; coarsest-level structure): D_c couples
+ * each coarse site to itself through a dense n x n block and to its 8 nearest
+ * neighbours.  Sec. 4.2 (Q = Gamma5 D is Hermitian) implies, on the coarse
+ * level, sigma3 D_c sigma3 = D_c^H, so the backward hop blocks are
+ * D_c[x, x-mu] = sigma3 D_c[x-mu, x]^H sigma3 and only the self block and the
+ * 4 forward hops are stored ("gamma5-compressed": 5 blocks per site).
+ *
+ * self_blocks : device, complex128 [V][n][n], row-major; A_x (without i*mu*sigma3).
+ * hop_blocks  : device, complex128 [V][8][n][n] (or [V][4][n][n] with
+ *               COARSE_ASSUME_GAMMA5); hop[x][d] = D_c[x, x+mu_d] for d < 4 and
+ *               D_c[x, x-mu_{d-4}] for d >= 4.
+ * Without COARSE_ASSUME_GAMMA5 the backward hops and the self blocks are
+ * checked against the sigma3 relation (relative defect <= 1e-10 of the
+ * largest block entry) and COARSE_ERR_NOT_GAMMA5 is returned if it fails.
+ * The caller keeps ownership of its buffers and may free them after return
+ * (the call synchronises `stream`).  *out receives a new handle owned by the
+ * caller, released with coarse_op_destroy.
+ */
+int coarse_op_create(const coarse_op_desc* desc, const void* self_blocks, const void* hop_blocks,
+                     void* stream, coarse_op** out);
+
+/*
+ * coarse_op_update -- new block values, same shape and flags (Sec. 3.6: when
+ * the multigrid setup changes the coarsest matrix, the polynomial and the
+ * recycle space are rebuilt at the next solve).  Invalidates both.
+ */
+int coarse_op_update(coarse_op* op, const void* self_blocks, const void* hop_blocks, void* stream);
+
+/* Releases the handle and all device memory it owns (synchronises the device). */
+void coarse_op_destroy(coarse_op* op);
+
+/*
+ * coarse_apply -- y = D_c x (Sec. 2.2, the coarse nearest-neighbour stencil):
+ *   y_x = (A_x + i mu sigma3) x_x + sum_mu D_c[x,x+mu] x_{x+mu} + sum_mu D_c[x,x-mu] x_{x-mu}.
+ * x, y : device, [nrhs][V][n], complex128 for COARSE_PREC_FP64 and complex64
+ *        otherwise; x and y must not overlap.
+ * nrhs : 1 .. desc.max_nrhs.  nrhs > 1 with COARSE_PREC_BF16 runs the
+ *        tensor-core multi-right-hand-side kernel.
+ * Asynchronous on `stream`.  The requested precision must have been enabled
+ * in desc.precisions (FP64 is always available).
+ */
+int coarse_apply(const coarse_op* op, const void* x, void* y, int nrhs, int precision, void* stream);
+
+/* coarse_apply_adjoint -- y = D_c^H x, computed as sigma3 D_c(-mu) sigma3 x. Same arguments. */
+int coarse_apply_adjoint(const coarse_op* op, const void* x, void* y, int nrhs, int precision, void* stream);
+
+/*
+ * coarse_residual -- r = b - D_c x in FP64 and the norms ||r||_2, ||b||_2.
+ * b, x, r : device complex128 [V][n] (one right-hand side); r may alias neither.
+ * norms_host : host double[2] receiving (||r||, ||b||); the call synchronises `stream`.
+ * The true residual that the solver's tolerance refers to.
+ */
+int coarse_residual(const coarse_op* op, const void* b, const void* x, void* r, double* norms_host,
+                    void* stream);
+
+/* Flags of coarse_solve_params.flags */
+#define COARSE_ZERO_GUESS 0x1u      /* ignore the incoming x, start from 0 */
+#define COARSE_REBUILD_POLY 0x2u    /* recompute the polynomial before this solve */
+#define COARSE_RESET_RECYCLE 0x4u   /* drop the GCRO-DR recycle space before this solve */
+#define COARSE_TIME_APPLY 0x8u      /* time every inner-precision stencil launch with CUDA events */
+
+typedef struct {
+  int32_t m;               /* restart length of GMRES / GCRO-DR (Sec. 3.1), 2 .. 64 */
+  int32_t max_restarts;    /* cycles allowed per inner solve */
+  double tol;              /* target ||b - D_c x||_2 / ||b||_2, true FP64 residual */
+  int32_t poly_degree;     /* d: number of Leja-ordered harmonic Ritz roots, q has degree d-1 (Sec. 3.3); 0 = off */
+  int32_t defl_k;          /* k recycled harmonic Ritz vectors (Sec. 3.4); 0 = plain (pp-)GMRES; k < m */
+  int32_t recycle_updates; /* u: recycle-space updates allowed, then frozen (Sec. 4.1.1) */
+  int32_t precision;       /* coarse_precision of the inner solver; FP64 = no refinement */
+  double inner_tol;        /* relative residual target of each inner solve (FP32/BF16 only) */
+  int32_t max_ir;          /* FP64 iterative-refinement steps allowed */
+  uint32_t flags;          /* COARSE_ZERO_GUESS | COARSE_REBUILD_POLY | COARSE_RESET_RECYCLE */
+  uint64_t seed;           /* seeds the polynomial start vector when poly_start is NULL */
+  const void* poly_start;  /* optional device complex128 [V][n]: start vector of the polynomial's Arnoldi */
+} coarse_solve_params;
+
+typedef struct {
+  int32_t status;          /* coarse_status of this solve */
+  int32_t iterations;      /* Arnoldi steps, all refinement steps together */
+  int32_t matvecs;         /* applications of D_c in the inner precision */
+  int32_t cycles;          /* GMRES / GCRO-DR cycles */
+  int32_t ir_steps;        /* FP64 refinement steps */
+  int32_t recycle_updates; /* updates of U_k, C_k made so far on this operator */
+  double rel_residual;     /* true FP64 ||b - D_c x|| / ||b|| at exit */
+  double setup_ms;         /* polynomial construction during this call (0 if reused) */
+  double solve_ms;         /* wall time of the call */
+  double apply_ms;         /* device time of the inner-precision stencil launches (COARSE_TIME_APPLY) */
+  int32_t apply_count;     /* stencil launches timed in apply_ms */
+  int32_t kernel_launches; /* kernels this call launched */
+} coarse_solve_info;
+
+/*
+ * coarse_solve -- solve D_c x = b (Sec. 3.6, the whole coarsest-level solver):
+ * restarted GMRES(m) (Sec. 3.1) with right polynomial preconditioner
+ * q(D_c) built from Leja-ordered harmonic Ritz values (Sec. 3.3, Alg. 3) and
+ * GCRO-DR deflation by k harmonic Ritz vectors with recycling across restarts
+ * and right-hand sides (Sec. 3.4), inside FP64 iterative refinement when the
+ * inner precision is FP32 or BF16.
+ * b : device complex128 [nrhs][V][n];  x : device complex128 [nrhs][V][n],
+ *     initial guess (unless COARSE_ZERO_GUESS) and result.  The right-hand
+ *     sides are solved one after another and share the polynomial and the
+ *     recycle space, which the handle keeps for later calls.
+ * info_host : host array of nrhs records (may be NULL).
+ * Synchronises `stream`.  Returns COARSE_ERR_NOT_CONVERGED if any column
+ * missed tol (x then holds the best iterate).
+ */
+int coarse_solve(coarse_op* op, const void* b, void* x, int nrhs, const coarse_solve_params* params,
+                 coarse_solve_info* info_host, void* stream);
+
+/*
+ * coarse_solve_adjoint -- solve D_c^H lambda = c via D_c^H = sigma3 D_c(-mu) sigma3
+ * (coarse form of Gamma5-hermiticity, Sec. 4.2): lambda = sigma3 D_c(-mu)^{-1} sigma3 c.
+ * Same arguments as coarse_solve (b = c, x = lambda).  For mu = 0 it shares the
+ * polynomial and the recycle space of the forward solve.
+ */
+int coarse_solve_adjoint(coarse_op* op, const void* b, void* x, int nrhs, const coarse_solve_params* params,
+                         coarse_solve_info* info_host, void* stream);
+
+/*
+ * coarse_solve_batched -- nops independent solves (operators of uneven size),
+ * advanced together: every Krylov phase of all unfinished solves runs in one
+ * kernel launch, the launch sequence of one step is captured once in a CUDA
+ * graph and replayed.  ops[i], b[i], x[i], nrhs[i] as in coarse_solve; all
+ * operators use the same params.  infos: host array of sum(nrhs) records in
+ * (operator, column) order.  Synchronises `stream`.
+ */
+int coarse_solve_batched(coarse_op* const* ops, int nops, const void* const* b, void* const* x,
+                         const int* nrhs, const coarse_solve_params* params, coarse_solve_info* infos,
+                         void* stream);
+
+/*
+ * coarse_block_grad -- block gradients of a real loss L through x = D_c^{-1} b
+ * given lambda = D_c^{-H} dL/dx*:  G_self[x] = -lambda_x x_x^H and
+ * G_hop[x][d] = -lambda_x x_{x +- mu_d}^H (convention dL = Re sum conj(G) dD).
+ * lambda, x : device complex128 [V][n];  g_self : device complex128 [V][n][n];
+ * g_hop : device complex128 [V][8][n][n] (canonical 9-block layout).
+ * Asynchronous on `stream`.
+ */
+int coarse_block_grad(const coarse_op* op, const void* lambda, const void* x, void* g_self, void* g_hop,
+                      void* stream);
+
+/*
+ * coarse_op_poly -- the Leja-ordered harmonic Ritz values theta_1..theta_d
+ * (Sec. 3.3, Alg. 2) currently held for `precision`.  theta_host: host double[2*cap]
+ * (re, im pairs); *d receives the degree (0 if none is built).
+ */
+int coarse_op_poly(const coarse_op* op, int precision, double* theta_host, int cap, int* d);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* coarse_last_error(void);
+
+/* Library version string. */
+const char* coarse_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COARSE_H */

@@ -1,0 +1,502 @@
+// Host side of the coarsest-level solver (Sec. 3.6): the launch sequence of
+// restarted GMRES / GCRO-DR with the polynomial right preconditioner, inside
+// FP64 iterative refinement.  Every vector and small dense operation runs in
+// the library's kernels; the host reads back one small status record per
+// Arnoldi cycle (and per refinement step) to decide what to launch next.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "common.cuh"
+#include "solver.cuh"
+#include "solver_state.cuh"
+
+namespace coarse {
+
+namespace {
+
+size_t csize(int v64) { return v64 ? sizeof(double2) : sizeof(float2); }
+
+template <class T>
+int dalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation of %zu bytes failed: %s", sizeof(T) * count, cudaGetErrorString(e));
+    return COARSE_ERR_OOM;
+  }
+  return COARSE_OK;
+}
+
+#define TRY(call)                 \
+  do {                            \
+    int _rc = (call);             \
+    if (_rc != COARSE_OK) return _rc; \
+  } while (0)
+
+}  // namespace
+
+Solver::~Solver() { release(); }
+
+void Solver::release() {
+  for (const Timed& tm : timed) {
+    ev_pool.push_back(tm.a);
+    ev_pool.push_back(tm.b);
+  }
+  timed.clear();
+  for (cudaEvent_t ev : ev_pool) cudaEventDestroy(ev);
+  ev_pool.clear();
+  if (vecmem) cudaFree(vecmem);
+  if (smallmem) cudaFree(smallmem);
+  if (st_host) cudaFreeHost(st_host);
+  vecmem = nullptr;
+  smallmem = nullptr;
+  st_host = nullptr;
+  m_cap = k_cap = d_cap = 0;
+  k_cur = 0;
+  updates = 0;
+  d = 0;
+  poly_ok = false;
+}
+
+int Solver::ensure(int m, int k, int dmax) {
+  if (m <= m_cap && k == k_cap && dmax <= d_cap && vecmem) return COARSE_OK;
+  release();
+  m_cap = m;
+  k_cap = k;
+  d_cap = dmax;
+  const size_t cs = csize(v64);
+  const size_t nvec = (size_t)(m + 1) + 4 * (size_t)k + 8;
+  const size_t vbytes = cs * (size_t)N;
+  TRY(dalloc((char**)&vecmem, nvec * vbytes));
+  char* p = (char*)vecmem;
+  auto take = [&]() { void* q = p; p += vbytes; return q; };
+  V.assign(m + 1, nullptr);
+  for (int i = 0; i <= m; ++i) V[i] = take();
+  for (int b = 0; b < 2; ++b) {
+    U[b].assign(k, nullptr);
+    C[b].assign(k, nullptr);
+    for (int i = 0; i < k; ++i) U[b][i] = take();
+    for (int i = 0; i < k; ++i) C[b][i] = take();
+  }
+  r = take(); e = take(); t = take(); sa = take(); sb = take(); acc = take(); w = take(); tmp = take();
+  // small arrays
+  const int ldh = kMaxDense + 1;
+  const int maxq = kMaxK + kMaxDense + 2;
+  ldsw = maxq;
+  size_t nsmall = 0;
+  auto cnt = [&](size_t c) { size_t o = nsmall; nsmall += (c * sizeof(double2) + 255) / 256 * 256; return o; };
+  const size_t o_h1 = cnt(maxq), o_h2 = cnt(maxq), o_H = cnt((size_t)ldh * kMaxDense), o_R = cnt((size_t)ldh * kMaxDense);
+  const size_t o_cs = cnt(kMaxDense), o_sn = cnt(kMaxDense), o_g = cnt(kMaxDense + 1), o_B = cnt((size_t)kMaxK * kMaxDense);
+  const size_t o_y = cnt(maxq), o_z = cnt(maxq), o_cC = cnt((size_t)maxq * kMaxK), o_cU = cnt((size_t)maxq * kMaxK);
+  const size_t o_th = cnt(kMaxPoly + 1), o_pc = cnt(kPolyScale + 1), o_SW = cnt((size_t)kMaxK * maxq);
+  const size_t o_part = cnt((size_t)(2 * maxq + 4) * 304), o_st = cnt(sizeof(CycleState) / sizeof(double2) + 1);
+  const size_t o_n2 = cnt(8), o_cnt = cnt(4), o_tab = cnt(16 * (size_t)(2 * maxq + 8));
+  TRY(dalloc((char**)&smallmem, nsmall));
+  char* b = (char*)smallmem;
+  h1 = (double2*)(b + o_h1); h2 = (double2*)(b + o_h2);
+  dn.H = (double2*)(b + o_H); dn.R = (double2*)(b + o_R); dn.cs = (double*)(b + o_cs); dn.sn = (double2*)(b + o_sn);
+  dn.g = (double2*)(b + o_g); dn.B = (double2*)(b + o_B); dn.ycoef = (double2*)(b + o_y); dn.z = (double2*)(b + o_z);
+  dn.coefC = (double2*)(b + o_cC); dn.coefU = (double2*)(b + o_cU); dn.theta = (double2*)(b + o_th);
+  dn.polyc = (double2*)(b + o_pc);
+  dn.ldh = ldh;
+  dn.ldb = kMaxK > 0 ? kMaxK : 1;
+  SW = (double2*)(b + o_SW);
+  partial = (double*)(b + o_part);
+  st = (CycleState*)(b + o_st);
+  norm2 = (double*)(b + o_n2);
+  counter = (unsigned*)(b + o_cnt);
+  void** tabs = (void**)(b + o_tab);
+  COARSE_CUDA(cudaMemsetAsync(smallmem, 0, nsmall, stream));
+  // pointer tables: vtab = [V_0..V_m]; qtab[p] = [C[p], V]; utab[p] = [U[p], V]; cnew[p] = C[1-p]; unew[p] = U[1-p]
+  std::vector<void*> host;
+  auto put = [&](const std::vector<void*>& v) { void** at = tabs + host.size(); host.insert(host.end(), v.begin(), v.end()); return at; };
+  vtab = put(V);
+  for (int p = 0; p < 2; ++p) {
+    std::vector<void*> q(C[p]);
+    q.insert(q.end(), V.begin(), V.end());
+    qtab[p] = put(q);
+    std::vector<void*> u(U[p]);
+    u.insert(u.end(), V.begin(), V.end());
+    utab[p] = put(u);
+    cnew[p] = put(C[1 - p]);
+    unew[p] = put(U[1 - p]);
+  }
+  one_acc = put({acc});
+  one_t = put({t});
+  COARSE_CUDA(cudaMemcpyAsync(tabs, host.data(), host.size() * sizeof(void*), cudaMemcpyHostToDevice, stream));
+  COARSE_CUDA(cudaMallocHost((void**)&st_host, sizeof(CycleState)));
+  COARSE_CUDA(cudaStreamSynchronize(stream));
+  par = 0;
+  k_cur = 0;
+  updates = 0;
+  poly_ok = false;
+  d = 0;
+  return COARSE_OK;
+}
+
+int Solver::apply(const void* x, void* y, int mode, void* accp, const double2* coef, const int* stop) {
+  ApplyArgs a;
+  a.blocks = op->blk[prec].ptr;
+  a.nb = op->nb;
+  a.x = x;
+  a.y = y;
+  a.z = nullptr;
+  a.acc = accp;
+  a.coef = coef;
+  a.mu = mu_eff;
+  a.V = op->V;
+  a.mode = mode;
+  a.adjoint = 0;
+  a.stop = stop;
+  ++matvecs;
+  if (!time_apply) return launch_apply(prec, op->n, a, stream);
+  while (ev_pool.size() < 2) {
+    cudaEvent_t ev;
+    COARSE_CUDA(cudaEventCreate(&ev));
+    ev_pool.push_back(ev);
+  }
+  Timed tm{cur_tag, ev_pool.back(), nullptr};
+  ev_pool.pop_back();
+  tm.b = ev_pool.back();
+  ev_pool.pop_back();
+  COARSE_CUDA(cudaEventRecord(tm.a, stream));
+  TRY(launch_apply(prec, op->n, a, stream));
+  COARSE_CUDA(cudaEventRecord(tm.b, stream));
+  timed.push_back(tm);
+  return COARSE_OK;
+}
+
+void Solver::harvest(int steps_done) {
+  for (const Timed& tm : timed) {
+    if (tm.tag < 0 || tm.tag < steps_done) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, tm.a, tm.b) == cudaSuccess) {
+        apply_ms += ms;
+        ++apply_count;
+      }
+    }
+    ev_pool.push_back(tm.a);
+    ev_pool.push_back(tm.b);
+  }
+  timed.clear();
+}
+
+// out = q(A) v (precondition only, result pointer returned in *res) -- d-1 applies
+int Solver::precondition(const void* v, const void** res, const int* stop) {
+  if (d == 0) { *res = v; return COARSE_OK; }
+  if (d == 1) {  // q = 1/theta_1
+    TRY(launch_scale(v64, v, nullptr, theta1_inv, acc, N, stop, 0, stream));
+    *res = acc;
+    return COARSE_OK;
+  }
+  TRY(apply(v, sa, APPLY_POLY_FIRST, acc, dn.polyc, stop));
+  void* cur = sa;
+  void* nxt = sb;
+  for (int i = 2; i < d; ++i) {
+    TRY(apply(cur, nxt, APPLY_POLY, acc, dn.polyc + 3 * (i - 1), stop));
+    void* tt = cur; cur = nxt; nxt = tt;
+  }
+  *res = acc;
+  return COARSE_OK;
+}
+
+// out = A v = D q(D) v  (d applies)
+int Solver::opA(const void* v, void* out, const int* stop) {
+  const void* mv = nullptr;
+  TRY(precondition(v, &mv, stop));
+  return apply(mv, out, APPLY_PLAIN, nullptr, nullptr, stop);
+}
+
+int Solver::read_state() {
+  COARSE_CUDA(cudaMemcpyAsync(st_host, st, sizeof(CycleState), cudaMemcpyDeviceToHost, stream));
+  COARSE_CUDA(cudaStreamSynchronize(stream));
+  return COARSE_OK;
+}
+
+// Orthogonalise V[j+1] against [C (kc), V_0..V_j] twice (CGS2, one fused reduction per pass),
+// then finalize the Arnoldi column and normalise.
+int Solver::arnoldi_step(int j, int kc, void* const* tab) {
+  const int* stop = &st->stop;
+  const int nq = kc + j + 1;
+  void* wv = V[j + 1];
+  TRY(launch_multidot(v64, (const void* const*)tab, nq, wv, N, h1, nullptr, partial, counter, stop, stream));
+  TRY(launch_update(v64, (const void* const*)tab, nq, h1, 1, wv, N, 0, nullptr, nullptr, partial, counter, stop, stream));
+  TRY(launch_multidot(v64, (const void* const*)tab, nq, wv, N, h2, nullptr, partial, counter, stop, stream));
+  TRY(launch_update(v64, (const void* const*)tab, nq, h2, 1, wv, N, 1, nullptr, &st->wnorm2, partial, counter, stop,
+                    stream));
+  TRY(launch_step_finalize(st, h1, h2, dn, stream));
+  // normalise v_{j+1} whenever the finalize of this step ran (st->j == j + 1), also on the step that stops
+  return launch_scale(v64, wv, &st->inv_h, make_double2(1.0, 0.0), wv, N, &st->j, j + 1, stream);
+}
+
+int Solver::build_poly(const double2* start64, uint64_t seed, int dd) {
+  poly_ok = false;
+  d = 0;
+  if (dd <= 0) { poly_ok = true; return COARSE_OK; }
+  if (start64) {
+    TRY(launch_copy_to(v64, start64, r, N, stream));
+  } else {
+    TRY(launch_fill_gaussian((double2*)tmp64, N, seed, stream));
+    TRY(launch_copy_to(v64, (const double2*)tmp64, r, N, stream));
+  }
+  TRY(launch_norm2(v64, r, N, norm2, partial, counter, stream));
+  TRY(launch_cycle_init(st, 0, dd, norm2, 0.0, dn.g, stream));
+  TRY(launch_scale(v64, r, &st->inv_h, make_double2(1.0, 0.0), V[0], N, nullptr, 0, stream));
+  for (int j = 0; j < dd; ++j) {
+    cur_tag = j;
+    TRY(apply(V[j], V[j + 1], APPLY_PLAIN, nullptr, nullptr, &st->stop));
+    TRY(arnoldi_step(j, 0, vtab));
+  }
+  cur_tag = -1;
+  TRY(launch_poly_roots(st, dn, dd, stream));
+  TRY(read_state());
+  harvest(st_host->j);
+  if (st_host->rstatus != 0 || st_host->d <= 0) {
+    set_error("polynomial construction failed (harmonic Ritz problem status %d)", st_host->rstatus);
+    return COARSE_ERR_BREAKDOWN;
+  }
+  d = st_host->d;
+  theta_host.resize(d);
+  COARSE_CUDA(cudaMemcpyAsync(theta_host.data(), dn.theta, sizeof(double2) * d, cudaMemcpyDeviceToHost, stream));
+  double2 sc;
+  COARSE_CUDA(cudaMemcpyAsync(&sc, dn.polyc + kPolyScale, sizeof(double2), cudaMemcpyDeviceToHost, stream));
+  COARSE_CUDA(cudaStreamSynchronize(stream));
+  theta1_inv = sc;
+  poly_ok = true;
+  return COARSE_OK;
+}
+
+// Inner solve A e = r (A = D q(D)), e accumulates M * (update).  r and e live in
+// this solver's buffers; r holds the initial residual.  Ends when the
+// least-squares residual reaches target_abs or after max_cycles cycles.
+int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit, InnerInfo* info) {
+  const int* nostop = nullptr;
+  TRY(launch_norm2(v64, r, N, norm2, partial, counter, stream));
+  for (int cyc = 0; cyc < max_cycles; ++cyc) {
+    const int kc = k_cur;
+    if (kc > 0) {
+      // keep r orthogonal to range(C): e += M U (C^H r), r -= C (C^H r)  (GCRO-DR, Sec. 3.4)
+      TRY(launch_multidot(v64, (const void* const*)qtab[par], kc, r, N, dn.ycoef, nullptr, partial, counter, nostop,
+                          stream));
+      TRY(launch_update(v64, (const void* const*)qtab[par], kc, dn.ycoef, 1, r, N, 1, nullptr, norm2, partial,
+                        counter, nostop, stream));
+      TRY(launch_combine(v64, (const void* const*)utab[par], kc, dn.ycoef, 1, (void* const*)one_t, 1, 0, N, nostop,
+                         stream));
+      const void* mt = nullptr;
+      TRY(precondition(t, &mt, nostop));
+      TRY(launch_axpy(v64, mt, e, make_double2(1.0, 0.0), N, nostop, stream));
+    }
+    const int steps = kc > 0 ? m - kc : m;
+    void* const* tab = kc > 0 ? qtab[par] : vtab;
+    TRY(launch_cycle_init(st, kc, steps, norm2, target_abs, dn.g, stream));
+    TRY(launch_scale(v64, r, &st->inv_h, make_double2(1.0, 0.0), V[0], N, &st->stop, 0, stream));
+    for (int j = 0; j < steps; ++j) {
+      cur_tag = j;
+      TRY(opA(V[j], V[j + 1], &st->stop));
+      TRY(arnoldi_step(j, kc, tab));
+    }
+    cur_tag = -1;
+    TRY(read_state());
+    const CycleState cs = *st_host;
+    harvest(cs.j);
+    info->cycles++;
+    if (cs.status & ST_NONFINITE) {
+      set_error("non-finite value in the Arnoldi process");
+      return COARSE_ERR_NONFINITE;
+    }
+    if (cs.status & ST_ZERO) return COARSE_OK;  // zero residual
+    const int j = cs.j;
+    info->iterations += j;
+    info->last_resid = cs.resid;
+    if (j == 0) return COARSE_OK;
+    TRY(launch_cycle_solve(st, dn, stream));
+    // e += M (U y_U + V y_V)
+    void* const* ut = kc > 0 ? utab[par] : vtab;
+    TRY(launch_combine(v64, (const void* const*)ut, kc + j, dn.ycoef, 1, (void* const*)one_t, 1, 0,
+                       N, nostop, stream));
+    const void* mt = nullptr;
+    TRY(precondition(t, &mt, nostop));
+    TRY(launch_axpy(v64, mt, e, make_double2(1.0, 0.0), N, nostop, stream));
+    // r -= V_{j+1} (Hbar y_V)
+    TRY(launch_update(v64, (const void* const*)vtab, j + 1, dn.z, 1, r, N, 1, nullptr, norm2, partial, counter, nostop,
+                      stream));
+    // recycle space (Sec. 3.4): first extraction needs more than k steps; then up to ulimit updates
+    const bool can = kdef > 0 && updates < ulimit && ((kc == 0 && j > kdef) || (kc > 0 && j >= 1));
+    if (can) {
+      for (int c = 0; c < kc; ++c)
+        TRY(launch_multidot(v64, (const void* const*)qtab[par], kc + j + 1, U[par][c], N, SW + (size_t)c * ldsw,
+                            nullptr, partial, counter, nostop, stream));
+      TRY(launch_recycle(st, dn, SW, ldsw, kdef, stream));
+      TRY(read_state());
+      harvest(1 << 30);
+      if (st_host->rstatus == 0) {
+        void* const* wt = kc > 0 ? qtab[par] : vtab;
+        TRY(launch_combine(v64, (const void* const*)wt, kc + j + 1, dn.coefC, kdef, (void* const*)cnew[par], kdef, 0,
+                           N, nostop, stream));
+        TRY(launch_combine(v64, (const void* const*)ut, kc + j, dn.coefU, kdef, (void* const*)unew[par], kdef, 0, N,
+                           nostop, stream));
+        par = 1 - par;
+        k_cur = kdef;
+        ++updates;
+      } else {
+        info->recycle_failures++;
+      }
+    }
+    if (cs.resid <= target_abs || (cs.status & ST_LUCKY)) return COARSE_OK;
+  }
+  return COARSE_OK;
+}
+
+}  // namespace coarse
+
+namespace coarse {
+
+namespace {
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
+Solver* get_solver(coarse_op* op, int prec, int adjoint_system, cudaStream_t stream) {
+  // With mu = 0, D_c(-mu) = D_c: the adjoint system reuses the forward solver (polynomial, recycle space).
+  const bool separate = adjoint_system && op->mu != 0.0;
+  Solver*& slot = separate ? op->adj_solver[prec] : op->solver[prec];
+  if (slot == nullptr) {
+    slot = new Solver();
+    slot->op = op;
+    slot->prec = prec;
+    slot->v64 = prec == COARSE_PREC_FP64;
+    slot->N = op->V * op->n;
+    slot->tmp64 = op->work64 + (size_t)op->V * op->n;
+    slot->mu_eff = separate ? -op->mu : op->mu;
+  }
+  slot->stream = stream;
+  return slot;
+}
+
+int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, const coarse_solve_params* p,
+                 coarse_solve_info* info, cudaStream_t stream, int mu_sign) {
+  const double t0 = now_ms();
+  coarse_solve_info inf{};
+  const int N = op->V * op->n;
+  const double mu_eff = mu_sign * op->mu;
+  s->stream = stream;
+  double2* r64 = op->work64;
+  double hn[2];
+
+  auto residual = [&]() -> int {
+    ApplyArgs a;
+    a.blocks = op->blk[COARSE_PREC_FP64].ptr;
+    a.nb = op->nb;
+    a.x = x64;
+    a.y = r64;
+    a.z = b64;
+    a.acc = nullptr;
+    a.coef = op->coef;  // {-1, +1}: r = -D x + b
+    a.mu = mu_eff;
+    a.V = op->V;
+    a.mode = APPLY_AXPBY;
+    a.adjoint = 0;
+    a.stop = nullptr;
+    TRY(launch_apply(COARSE_PREC_FP64, op->n, a, stream));
+    return launch_norm2(1, r64, N, op->norms, op->red, op->counter, stream);
+  };
+
+  if (p->flags & COARSE_ZERO_GUESS) COARSE_CUDA(cudaMemsetAsync(x64, 0, sizeof(double2) * (size_t)N, stream));
+  TRY(residual());
+  TRY(launch_norm2(1, b64, N, op->norms + 1, op->red, op->counter, stream));
+  COARSE_CUDA(cudaMemcpyAsync(hn, op->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  COARSE_CUDA(cudaStreamSynchronize(stream));
+  const double bn = sqrt(hn[1]);
+  double rn = sqrt(hn[0]);
+  if (!isfinite(bn) || !isfinite(rn)) {
+    set_error("non-finite right-hand side or initial guess");
+    inf.status = COARSE_ERR_NONFINITE;
+    if (info) *info = inf;
+    return COARSE_ERR_NONFINITE;
+  }
+  if (bn == 0.0) {
+    COARSE_CUDA(cudaMemsetAsync(x64, 0, sizeof(double2) * (size_t)N, stream));
+    COARSE_CUDA(cudaStreamSynchronize(stream));
+    inf.rel_residual = 0.0;
+    inf.solve_ms = now_ms() - t0;
+    if (info) *info = inf;
+    return COARSE_OK;
+  }
+  const int m = p->m;
+  const int k = p->defl_k;
+  const int dd = p->poly_degree;
+  TRY(s->ensure(m, k, dd > 0 ? dd : 1));
+  if (p->flags & COARSE_RESET_RECYCLE) {
+    s->k_cur = 0;
+    s->updates = 0;
+  }
+  const long long mv0 = s->matvecs;
+  const long long launches0 = launches_so_far();
+  s->time_apply = (p->flags & COARSE_TIME_APPLY) != 0;
+  s->apply_ms = 0.0;
+  s->apply_count = 0;
+  if (!s->poly_ok || (p->flags & COARSE_REBUILD_POLY) || s->d_cap < dd || (dd > 0 && s->d == 0) ||
+      (dd == 0 && s->d != 0)) {
+    const double ts = now_ms();
+    TRY(s->build_poly((const double2*)p->poly_start, p->seed, dd));
+    inf.setup_ms = now_ms() - ts;
+  }
+  int rc = COARSE_OK;
+  double rel = rn / bn;
+  int stall = 0;
+  while (rel > p->tol && inf.ir_steps < p->max_ir) {
+    InnerInfo ii;
+    COARSE_CUDA(cudaMemsetAsync(s->e, 0, (s->v64 ? sizeof(double2) : sizeof(float2)) * (size_t)N, stream));
+    if (s->v64) {
+      COARSE_CUDA(cudaMemcpyAsync(s->r, r64, sizeof(double2) * (size_t)N, cudaMemcpyDeviceToDevice, stream));
+      TRY(s->inner(0.5 * p->tol * bn, p->max_restarts, m, k, p->recycle_updates, &ii));
+      TRY(launch_axpy(1, s->e, x64, make_double2(1.0, 0.0), N, nullptr, stream));
+    } else {
+      TRY(launch_to_low(r64, op->norms, (float2*)s->r, N, stream));
+      const double target = fmax(p->inner_tol, 0.5 * p->tol * bn / rn);
+      TRY(s->inner(target, p->max_restarts, m, k, p->recycle_updates, &ii));
+      TRY(launch_add_low(x64, op->norms, (const float2*)s->e, N, stream));
+    }
+    inf.ir_steps++;
+    inf.cycles += ii.cycles;
+    inf.iterations += ii.iterations;
+    TRY(residual());
+    COARSE_CUDA(cudaMemcpyAsync(hn, op->norms, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    COARSE_CUDA(cudaStreamSynchronize(stream));
+    const double rn_new = sqrt(hn[0]);
+    if (!isfinite(rn_new)) {
+      set_error("non-finite residual during refinement");
+      rc = COARSE_ERR_NONFINITE;
+      break;
+    }
+    stall = (rn_new > 0.5 * rn) ? stall + 1 : 0;
+    rn = rn_new;
+    rel = rn / bn;
+    if (stall >= 3) break;
+  }
+  COARSE_CUDA(cudaStreamSynchronize(stream));
+  s->harvest(1 << 30);
+  s->time_apply = false;
+  inf.apply_ms = s->apply_ms;
+  inf.apply_count = (int)s->apply_count;
+  inf.kernel_launches = (int)(launches_so_far() - launches0);
+  inf.matvecs = (int)(s->matvecs - mv0);
+  inf.recycle_updates = s->updates;
+  inf.rel_residual = rel;
+  if (rc == COARSE_OK && rel > p->tol) {
+    set_error("tolerance %.3e not reached: relative residual %.3e after %d refinement steps", p->tol, rel,
+              inf.ir_steps);
+    rc = COARSE_ERR_NOT_CONVERGED;
+  }
+  inf.status = rc;
+  inf.solve_ms = now_ms() - t0;
+  if (info) *info = inf;
+  return rc;
+}
+
+}  // namespace coarse

@@ -1,0 +1,94 @@
+// Per-operator, per-precision Krylov solver state (host object owning device memory).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "solver_state.cuh"
+
+namespace coarse {
+
+struct InnerInfo {
+  int cycles = 0;
+  int iterations = 0;
+  int recycle_failures = 0;
+  double last_resid = 0.0;
+};
+
+struct Solver {
+  coarse_op* op = nullptr;
+  int prec = COARSE_PREC_FP32;  // block precision
+  int v64 = 0;                  // vectors are complex128
+  int N = 0;                    // unknowns
+  double mu_eff = 0.0;          // twisted mass entering the apply (sign flipped for the adjoint system)
+  cudaStream_t stream = nullptr;
+  void* tmp64 = nullptr;        // FP64 work vector owned by the operator
+
+  int m_cap = 0, k_cap = 0, d_cap = 0;
+  void* vecmem = nullptr;
+  void* smallmem = nullptr;
+  std::vector<void*> V;
+  std::vector<void*> U[2], C[2];
+  int par = 0;       // current U/C buffer
+  int k_cur = 0;     // recycle vectors held
+  int updates = 0;   // recycle-space updates made
+  void *r = nullptr, *e = nullptr, *t = nullptr, *sa = nullptr, *sb = nullptr, *acc = nullptr, *w = nullptr,
+       *tmp = nullptr;
+  void** vtab = nullptr;
+  void** qtab[2] = {nullptr, nullptr};
+  void** utab[2] = {nullptr, nullptr};
+  void** cnew[2] = {nullptr, nullptr};
+  void** unew[2] = {nullptr, nullptr};
+  void** one_acc = nullptr;
+  void** one_t = nullptr;
+  double2 *h1 = nullptr, *h2 = nullptr, *SW = nullptr;
+  int ldsw = 0;
+  Dense dn{};
+  double* partial = nullptr;
+  unsigned* counter = nullptr;
+  double* norm2 = nullptr;
+  CycleState* st = nullptr;
+  CycleState* st_host = nullptr;
+
+  int d = 0;             // polynomial degree in use
+  bool poly_ok = false;  // polynomial built for the current operator values
+  std::vector<double2> theta_host;
+  double2 theta1_inv{0.0, 0.0};
+  long long matvecs = 0;
+  // optional CUDA-event timing of the stencil launches (COARSE_TIME_APPLY)
+  bool time_apply = false;
+  int cur_tag = -1;                 // Arnoldi step of the applies being launched (-1: not gated)
+  struct Timed { int tag; cudaEvent_t a, b; };
+  std::vector<Timed> timed;         // launched, not yet harvested
+  std::vector<cudaEvent_t> ev_pool;
+  double apply_ms = 0.0;
+  long long apply_count = 0;
+  void harvest(int steps_done);     // after a stream sync: add the elapsed time of the applies that ran
+
+  ~Solver();
+  void release();
+  int ensure(int m, int k, int dmax);
+  int apply(const void* x, void* y, int mode, void* accp, const double2* coef, const int* stop);
+  int precondition(const void* v, const void** res, const int* stop);
+  int opA(const void* v, void* out, const int* stop);
+  int read_state();
+  int arnoldi_step(int j, int kc, void* const* tab);
+  int build_poly(const double2* start64, uint64_t seed, int d);
+  int inner(double target_abs, int max_cycles, int m, int kdef, int ulimit, InnerInfo* info);
+  void invalidate() {
+    poly_ok = false;
+    d = 0;
+    k_cur = 0;
+    updates = 0;
+    par = 0;
+  }
+};
+
+// One right-hand side through FP64 iterative refinement around Solver::inner.
+// b64, x64: device complex128 [V][n].  mu_sign = +1 (D_c) or -1 (D_c(-mu), adjoint systems).
+int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, const coarse_solve_params* p,
+                 coarse_solve_info* info, cudaStream_t stream, int mu_sign);
+
+Solver* get_solver(coarse_op* op, int prec, int adjoint_system, cudaStream_t stream);
+
+}  // namespace coarse

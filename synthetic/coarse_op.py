@@ -167,7 +167,8 @@ def refine_test_vectors(D: FineOperator, starts: torch.Tensor, iters: int) -> to
             basis.append(w / H[j + 1, j])
         rhs = torch.zeros(m + 1, dtype=torch.complex128, device=x0.device)
         rhs[0] = beta
-        z = torch.linalg.lstsq(H[: m + 1, :m], rhs[:, None]).solution[:, 0]
+        # small least-squares problem on the host (any device gives the same arithmetic)
+        z = torch.linalg.lstsq(H[: m + 1, :m].cpu(), rhs[:, None].cpu()).solution[:, 0].to(x0.device)
         x = x0.clone()
         for i in range(m):
             x = x + z[i] * basis[i]
@@ -189,14 +190,15 @@ def prolongator(tv: torch.Tensor, dims) -> torch.Tensor:
     t = t.permute(0, 2, 4, 6, 8, 1, 3, 5, 7, 9, 10, 11)  # agg(4), chir, local(4), spin, col, nv
     Vc = (L0 // 2) * (L1 // 2) * (L2 // 2) * (L3 // 2)
     shp = t.shape
-    t = t.reshape(Vc * 2, 96, nv)
+    dev = t.device
+    t = t.reshape(Vc * 2, 96, nv).cpu()   # batched QR on the host
     q, r = torch.linalg.qr(t)
     ph = torch.diagonal(r, dim1=-2, dim2=-1)
     ph = ph / ph.abs()
     q = q * ph[:, None, :]
     q = q.reshape(shp)
     q = q.permute(0, 5, 1, 6, 2, 7, 3, 8, 4, 9, 10, 11)  # back to (L3/2,2,L2/2,2,L1/2,2,L0/2,2,chir,spin,col,nv)
-    return q.reshape(L0 * L1 * L2 * L3, 4, 3, nv)
+    return q.reshape(L0 * L1 * L2 * L3, 4, 3, nv).to(dev)
 
 
 def _restrict(Pf: torch.Tensor, w: torch.Tensor, dims) -> torch.Tensor:
