@@ -126,17 +126,32 @@ def run_gb300(args):
     # replicas: each rank solves its own right-hand sides with its own copy of the operator
     op = build_coarse_operator(KEY, FINE_DIMS, NV, M0, CSW, device=dev)
     cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(prec,))
+    host_blocks = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        host_blocks = (op.self_blocks.cpu().numpy(), op.hop_blocks.cpu().numpy(), op.dims)
     del op
     torch.cuda.empty_cache()
     n, V = 2 * NV, cop.V
     N = V * n
     total = args.warmup + 2 * args.steps
     B = torch.from_numpy(draws.rhs((*KEY, 100 + rank), total, N)).to(dev)
+    S = torch.from_numpy(draws.rhs((*KEY, 50 + rank), 4, N)).to(dev)  # setup right-hand sides
     X = torch.zeros_like(B)
     inner_tol = 1e-5 if prec == cg.PREC_FP32 else 1e-2
     p = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS, **PARAMS)
     pt = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS | cg.COARSE_TIME_APPLY,
                          **PARAMS)
+    # setup: the polynomial and the first u recycle-space updates (after u updates U_k, C_k
+    # stay frozen for all later solves with this operator, Sec. 4.1.1); reported separately
+    t_setup = time.perf_counter()
+    setup_solves = 0
+    for i in range(40):
+        _, inf = cop.solve(S[i % S.shape[0]], X[0], params=p)
+        setup_solves += 1
+        if inf[0]["recycle_updates"] >= PARAMS["recycle_updates"]:
+            break
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
     for i in range(args.warmup):
         cop.solve(B[i], X[i], params=p)
     torch.cuda.synchronize()
@@ -147,11 +162,13 @@ def run_gb300(args):
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for i in range(args.steps):
             _, inf = cop.solve(B[args.warmup + i], X[args.warmup + i], params=pt)
             infos.append(inf[0])
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         barrier()
     ms = e0.elapsed_time(e1)
@@ -218,11 +235,31 @@ def run_gb300(args):
                      "launches_timed": apply_cnt, "peak_source": src},
         "solver": {"iterations_per_solve": iters, "matvecs_per_solve": statistics.mean(i["matvecs"] for i in infos),
                    "ir_steps": statistics.mean(i["ir_steps"] for i in infos), "worst_rel_residual": worst_res,
-                   "recycle_updates": infos[-1]["recycle_updates"]},
+                   "recycle_updates": infos[-1]["recycle_updates"],
+                   "setup": {"solves": setup_solves, "seconds": round(t_setup, 3),
+                             "what": "polynomial + recycle-space updates until u=10 is reached"}},
         "clocks": clk.summary(),
     }
+    if args.fp64_baseline_steps > 0:
+        # plain FP64 GPU GMRES(50) on the same right-hand sides: the reference point of the speedup
+        p64 = cg.solve_params(precision=cg.PREC_FP64, m=PARAMS["m"], tol=PARAMS["tol"], max_restarts=2000,
+                              max_ir=5, flags=cg.COARSE_ZERO_GUESS)
+        nb = args.fp64_baseline_steps
+        cop.solve(B[0], X[0], params=p64)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        its64 = []
+        for i in range(nb):
+            _, inf = cop.solve(B[args.warmup + i], X[args.warmup + i], params=p64)
+            its64.append(inf[0]["iterations"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v64 = nb / (e0.elapsed_time(e1) / 1e3)
+        line["fp64_gmres_baseline"] = {"value": round(v64, 4), "unit": "solves/s", "steps": nb,
+                                       "iterations_per_solve": statistics.mean(its64),
+                                       "speedup": round(value / world / v64, 2)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cop, iters, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(host_blocks, iters)
     if rank == 0:
         print(json.dumps(line), flush=True)
     cop.close()
@@ -263,11 +300,10 @@ def oracle_iterations():
         return None, None
 
 
-def cpu_baseline(cop, gpu_iters, budget_s=20.0):
-    op = oracle_workload()
-    s, h = op.self_blocks.numpy(), op.hop_blocks.numpy()
+def cpu_baseline(host_blocks, gpu_iters):
+    s, h, dims = host_blocks
     steps = 8
-    per_step = oracle_sample(s, h, op.dims, budget_s, steps)
+    per_step = oracle_sample(s, h, dims, 0, steps)
     iters, src = oracle_iterations()
     if iters is None:
         iters, src = gpu_iters, "Arnoldi steps per solve of this run"
@@ -306,16 +342,79 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+APPLY_CASES = {
+    # name: (fine dims, nv, m0, mu, description)
+    "wilson8": ((16, 16, 16, 16), 16, -0.42, 0.0, "wilson-clover coarse 8^4, n=32"),
+    "tm16": ((32, 32, 32, 32), 24, -0.42, 3e-3, "twisted mass coarse 16^4, n=48, mu=3e-3"),
+    "tm12": ((24, 24, 24, 24), 24, -0.42, 3e-3, "twisted mass coarse 12^4, n=48, mu=3e-3 (profiling size)"),
+}
+
+
+def run_apply_only(args):
+    """Stencil apply alone: achieved algorithmic GB/s with an L2 flush (256 MB write) between launches."""
+    import torch
+
+    import paper_2205_09104_gb300 as cg
+    from synthetic.coarse_op import build_coarse_operator
+    fine, nv, m0, mu, desc = APPLY_CASES[args.apply_only]
+    prec = {"fp64": cg.PREC_FP64, "fp32": cg.PREC_FP32, "bf16": cg.PREC_BF16}[args.prec]
+    dev = torch.device("cuda", 0)
+    op = build_coarse_operator((3, 0), fine, nv, m0, CSW, device=dev)
+    cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, mu=mu,
+                      precisions=(prec,) if prec else ())
+    del op
+    torch.cuda.empty_cache()
+    n, V = 2 * nv, cop.V
+    N = n * V
+    dt = torch.complex128 if prec == cg.PREC_FP64 else torch.complex64
+    g = torch.Generator(device="cpu").manual_seed(5)
+    x = torch.randn(N, dtype=dt, generator=g).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        cop.apply(x, precision=prec)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        if not args.no_flush:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        y = cop.apply(x, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    esize = {cg.PREC_FP64: 16, cg.PREC_FP32: 8, cg.PREC_BF16: 4}[prec]
+    vsize = 16 if prec == cg.PREC_FP64 else 8
+    nbytes = 5 * n * n * V * esize + 2 * N * vsize
+    flops = 9 * n * n * 8 * V
+    med = statistics.median(ts)
+    peak, src = peaks()
+    print(json.dumps({"mode": "apply", "case": args.apply_only, "workload": desc, "precision": args.prec,
+                      "l2_flush": not args.no_flush, "median_us": round(med * 1e3, 2), "min_us": round(min(ts) * 1e3, 2),
+                      "bytes_per_launch": nbytes, "achieved_gbs": round(nbytes / (med * 1e-3) / 1e9, 1),
+                      "peak_gbs": peak, "frac": round(nbytes / (med * 1e-3) / 1e9 / peak, 4), "peak_source": src,
+                      "gflops": round(flops / (med * 1e-3) / 1e9, 1), "launches": len(ts)}), flush=True)
+    cop.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--apply-only", choices=sorted(APPLY_CASES), default=None,
+                    help="time the stencil apply alone on one of the named lattices")
+    ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--fp64-baseline-steps", type=int, default=2,
+                    help="plain FP64 GMRES(50) solves timed for the speedup (0 = skip)")
     args = ap.parse_args()
+    if args.apply_only:
+        run_apply_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

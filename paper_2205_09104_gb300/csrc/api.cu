@@ -66,6 +66,8 @@ void free_op(coarse_op* op) {
   if (op->nb) cudaFree(op->nb);
   if (op->work64) cudaFree(op->work64);
   if (op->red) cudaFree(op->red);
+  if (op->apply_scratch) cudaFree(op->apply_scratch);
+  if (op->apply_cnt) cudaFree(op->apply_cnt);
   delete op;
 }
 
@@ -148,19 +150,9 @@ int apply_impl(const coarse_op* op, const void* x, void* y, int nrhs, int precis
   const size_t esz = precision == COARSE_PREC_FP64 ? sizeof(double2) : sizeof(float2);
   const size_t col = esz * (size_t)op->V * op->n;
   for (int c = 0; c < nrhs; ++c) {
-    ApplyArgs a;
-    a.blocks = op->blk[precision].ptr;
-    a.nb = op->nb;
-    a.x = (const char*)x + c * col;
-    a.y = (char*)y + c * col;
-    a.z = nullptr;
-    a.acc = nullptr;
-    a.coef = nullptr;
+    ApplyArgs a = make_apply_args(op, precision, (const char*)x + c * col, (char*)y + c * col);
     a.mu = adjoint ? -op->mu : op->mu;
-    a.V = op->V;
-    a.mode = APPLY_PLAIN;
     a.adjoint = adjoint;
-    a.stop = nullptr;
     TRY(launch_apply(precision, op->n, a, s));
   }
   return COARSE_OK;
@@ -272,6 +264,8 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
     CREATE_TRY(dmalloc((char**)&op->blk[p].ptr, op->blk[p].bytes));
   }
   CREATE_TRY(dmalloc(&op->work64, 3 * N * sizeof(double2)));
+  CREATE_TRY(dmalloc((char**)&op->apply_scratch, 5 * N * sizeof(double2)));
+  CREATE_TRY(dmalloc(&op->apply_cnt, ((size_t)op->V + 4) * sizeof(int)));
   CREATE_TRY(dmalloc((char**)&op->red, (2 * 304 + 64) * sizeof(double) + 64));
   op->norms = op->red + 2 * 304;
   op->coef = (double2*)(op->norms + 8);
@@ -279,6 +273,7 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
   const double2 cst[2] = {make_double2(-1.0, 0.0), make_double2(1.0, 0.0)};
   if (cudaMemcpyAsync(op->nb, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(op->red, 0, (2 * 304 + 64) * sizeof(double) + 64, s) != cudaSuccess ||
+      cudaMemsetAsync(op->apply_cnt, 0, ((size_t)op->V + 4) * sizeof(int), s) != cudaSuccess ||
       cudaMemcpyAsync(op->coef, cst, sizeof(cst), cudaMemcpyHostToDevice, s) != cudaSuccess) {
     cuda_fail(cudaGetLastError(), "coarse_op_create copies");
     free_op(op);
@@ -321,19 +316,10 @@ int coarse_residual(const coarse_op* op, const void* b, const void* x, void* r, 
   if (r == x || r == b) { set_error("r must not alias b or x"); return COARSE_ERR_INVALID_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
   const int N = op->V * op->n;
-  ApplyArgs a;
-  a.blocks = op->blk[COARSE_PREC_FP64].ptr;
-  a.nb = op->nb;
-  a.x = x;
-  a.y = r;
+  ApplyArgs a = make_apply_args(op, COARSE_PREC_FP64, x, r);
   a.z = b;
-  a.acc = nullptr;
   a.coef = op->coef;
-  a.mu = op->mu;
-  a.V = op->V;
   a.mode = APPLY_AXPBY;
-  a.adjoint = 0;
-  a.stop = nullptr;
   TRY(launch_apply(COARSE_PREC_FP64, op->n, a, s));
   TRY(launch_norm2(1, r, N, op->norms + 4, op->red, op->counter, s));
   TRY(launch_norm2(1, b, N, op->norms + 5, op->red, op->counter, s));

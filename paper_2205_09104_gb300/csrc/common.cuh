@@ -85,6 +85,8 @@ struct coarse_op {
   double* norms = nullptr;          // device norms (||r||^2, ||b||^2, gamma5 defect, ...)
   double2* coef = nullptr;          // device constants: {-1, 1} for r = b - D x
   unsigned* counter = nullptr;      // last-block counter of the op-level reductions
+  void* apply_scratch = nullptr;    // 5 * V * n complex128: pull partials and pushes of the stencil
+  int* apply_cnt = nullptr;         // V arrival counters of the stencil (zero between launches), then an error flag
   int device = 0;
 };
 
@@ -112,9 +114,35 @@ struct ApplyArgs {
   int mode;
   int adjoint;          // 1: y = sigma3 D(-mu) sigma3 x  (mu sign handled by caller), i.e. D^H
   const int* stop;      // optional device flag: return immediately if *stop != 0
+  void* part;           // scratch [V][n] pull partials (vector-accumulator type)
+  void* push;           // scratch [4][V][n] pushes to the forward neighbours
+  int* cnt;             // [V] arrival counters, zero between launches
+  int* err;             // raised (1) if a bounded wait of the TMA-staged kernel expired
 };
 
 int launch_apply(int prec, int n, const ApplyArgs& a, cudaStream_t s);
+
+// Arguments of a plain y = D x launch on operator `op` with the blocks of precision `prec`.
+inline ApplyArgs make_apply_args(const coarse_op* op, int prec, const void* x, void* y) {
+  ApplyArgs a;
+  a.blocks = op->blk[prec].ptr;
+  a.nb = op->nb;
+  a.x = x;
+  a.y = y;
+  a.z = nullptr;
+  a.acc = nullptr;
+  a.coef = nullptr;
+  a.mu = op->mu;
+  a.V = op->V;
+  a.mode = APPLY_PLAIN;
+  a.adjoint = 0;
+  a.stop = nullptr;
+  a.part = op->apply_scratch;
+  a.push = (char*)op->apply_scratch + (size_t)op->V * op->n * (prec == COARSE_PREC_FP64 ? 16 : 8);
+  a.cnt = op->apply_cnt;
+  a.err = op->apply_cnt + op->V;
+  return a;
+}
 int launch_apply_mrhs_bf16(const coarse_op* op, const void* x, void* y, int nrhs, int adjoint, cudaStream_t s);
 
 // ------------------------------------------------------------------ BLAS kernels

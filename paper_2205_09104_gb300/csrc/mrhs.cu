@@ -6,19 +6,9 @@ namespace coarse {
 int launch_apply_mrhs_bf16(const coarse_op* op, const void* x, void* y, int nrhs, int adjoint, cudaStream_t s) {
   const size_t col = sizeof(float2) * (size_t)op->V * op->n;
   for (int c = 0; c < nrhs; ++c) {
-    ApplyArgs a;
-    a.blocks = op->blk[COARSE_PREC_BF16].ptr;
-    a.nb = op->nb;
-    a.x = (const char*)x + c * col;
-    a.y = (char*)y + c * col;
-    a.z = nullptr;
-    a.acc = nullptr;
-    a.coef = nullptr;
+    ApplyArgs a = make_apply_args(op, COARSE_PREC_BF16, (const char*)x + c * col, (char*)y + c * col);
     a.mu = adjoint ? -op->mu : op->mu;
-    a.V = op->V;
-    a.mode = APPLY_PLAIN;
     a.adjoint = adjoint;
-    a.stop = nullptr;
     int rc = launch_apply(COARSE_PREC_BF16, op->n, a, s);
     if (rc != COARSE_OK) return rc;
   }

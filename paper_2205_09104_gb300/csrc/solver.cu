@@ -49,6 +49,8 @@ void Solver::release() {
   timed.clear();
   for (cudaEvent_t ev : ev_pool) cudaEventDestroy(ev);
   ev_pool.clear();
+  for (int i = 0; i < 2; ++i)
+    if (chunk_ev[i]) { cudaEventDestroy(chunk_ev[i]); chunk_ev[i] = nullptr; }
   if (vecmem) cudaFree(vecmem);
   if (smallmem) cudaFree(smallmem);
   if (st_host) cudaFreeHost(st_host);
@@ -128,7 +130,10 @@ int Solver::ensure(int m, int k, int dmax) {
   one_acc = put({acc});
   one_t = put({t});
   COARSE_CUDA(cudaMemcpyAsync(tabs, host.data(), host.size() * sizeof(void*), cudaMemcpyHostToDevice, stream));
-  COARSE_CUDA(cudaMallocHost((void**)&st_host, sizeof(CycleState)));
+  COARSE_CUDA(cudaMallocHost((void**)&st_host, sizeof(CycleState) + 4 * sizeof(int)));
+  stop_host = (int*)(st_host + 1);
+  for (int i = 0; i < 2; ++i)
+    if (!chunk_ev[i]) COARSE_CUDA(cudaEventCreateWithFlags(&chunk_ev[i], cudaEventDisableTiming));
   COARSE_CUDA(cudaStreamSynchronize(stream));
   par = 0;
   k_cur = 0;
@@ -139,18 +144,11 @@ int Solver::ensure(int m, int k, int dmax) {
 }
 
 int Solver::apply(const void* x, void* y, int mode, void* accp, const double2* coef, const int* stop) {
-  ApplyArgs a;
-  a.blocks = op->blk[prec].ptr;
-  a.nb = op->nb;
-  a.x = x;
-  a.y = y;
-  a.z = nullptr;
+  ApplyArgs a = make_apply_args(op, prec, x, y);
   a.acc = accp;
   a.coef = coef;
   a.mu = mu_eff;
-  a.V = op->V;
   a.mode = mode;
-  a.adjoint = 0;
   a.stop = stop;
   ++matvecs;
   if (!time_apply) return launch_apply(prec, op->n, a, stream);
@@ -294,15 +292,32 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
     void* const* tab = kc > 0 ? qtab[par] : vtab;
     TRY(launch_cycle_init(st, kc, steps, norm2, target_abs, dn.g, stream));
     TRY(launch_scale(v64, r, &st->inv_h, make_double2(1.0, 0.0), V[0], N, &st->stop, 0, stream));
-    for (int j = 0; j < steps; ++j) {
-      cur_tag = j;
-      TRY(opA(V[j], V[j + 1], &st->stop));
-      TRY(arnoldi_step(j, kc, tab));
+    // Steps go out in chunks; the stop flag of chunk c-1 is read back (async copy +
+    // event) while chunk c runs, so at most one chunk of gated launches follows a stop.
+    constexpr int kChunk = 4;
+    int pending = -1;  // chunk whose flag copy is in flight
+    int launched = 0;
+    for (int j0 = 0; j0 < steps; j0 += kChunk) {
+      for (int j = j0; j < steps && j < j0 + kChunk; ++j) {
+        ++launched;
+        cur_tag = j;
+        TRY(opA(V[j], V[j + 1], &st->stop));
+        TRY(arnoldi_step(j, kc, tab));
+      }
+      const int slot = (j0 / kChunk) & 1;
+      COARSE_CUDA(cudaMemcpyAsync(stop_host + slot, &st->stop, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      COARSE_CUDA(cudaEventRecord(chunk_ev[slot], stream));
+      if (pending >= 0) {
+        COARSE_CUDA(cudaEventSynchronize(chunk_ev[pending]));
+        if (stop_host[pending]) break;
+      }
+      pending = slot;
     }
     cur_tag = -1;
     TRY(read_state());
     const CycleState cs = *st_host;
     harvest(cs.j);
+    matvecs -= (long long)(launched - cs.j) * (d > 1 ? d : 1);  // gated steps did not run
     info->cycles++;
     if (cs.status & ST_NONFINITE) {
       set_error("non-finite value in the Arnoldi process");
@@ -389,19 +404,11 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
   double hn[2];
 
   auto residual = [&]() -> int {
-    ApplyArgs a;
-    a.blocks = op->blk[COARSE_PREC_FP64].ptr;
-    a.nb = op->nb;
-    a.x = x64;
-    a.y = r64;
+    ApplyArgs a = make_apply_args(op, COARSE_PREC_FP64, x64, r64);
     a.z = b64;
-    a.acc = nullptr;
     a.coef = op->coef;  // {-1, +1}: r = -D x + b
     a.mu = mu_eff;
-    a.V = op->V;
     a.mode = APPLY_AXPBY;
-    a.adjoint = 0;
-    a.stop = nullptr;
     TRY(launch_apply(COARSE_PREC_FP64, op->n, a, stream));
     return launch_norm2(1, r64, N, op->norms, op->red, op->counter, stream);
   };

@@ -49,6 +49,8 @@ struct Solver {
   double* norm2 = nullptr;
   CycleState* st = nullptr;
   CycleState* st_host = nullptr;
+  int* stop_host = nullptr;             // pinned: stop flags of the last two step chunks
+  cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
 
   int d = 0;             // polynomial degree in use
   bool poly_ok = false;  // polynomial built for the current operator values
