@@ -14,7 +14,6 @@ namespace coarse {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kGroup = 8;     // vectors per CTA row of the multi-dot
 constexpr int kMaxChunks = 304;
 
 template <class C> struct Acc;
@@ -85,101 +84,187 @@ __device__ bool last_block(unsigned* counter, unsigned total) {
   return is_last;
 }
 
-// h_i = <q_i, w> for i < nq and ||w||^2 (slot nq).  grid = (chunks, ceil((nq+1)/kGroup)).
-template <class C>
-__global__ void __launch_bounds__(kThreads) k_multidot(const C* const* q, int nq, const C* w, int N, double2* out,
-                                                       double* wnorm2, double* partial, unsigned* counter,
-                                                       const int* stop) {
-  if (stop != nullptr && *stop) return;
-  using T = typename Acc<C>::T;
-  __shared__ double sh[kThreads / 32 * 2 * kGroup];
+// Chunked layout of the Gram-Schmidt kernels: CTA = kW warps, warp chunk = 32*E contiguous
+// elements, lane owns elements chunk + lane + 32*e (coalesced for every e).  The w slice
+// stays in registers while the kernel sweeps all basis vectors.
+constexpr int kW = 8;
+constexpr int kMaxQ = 104;  // largest nq + 1 handled in one launch
+
+template <class C> __device__ __forceinline__ float2 to_f2(C v) { return make_float2(float(v.x), float(v.y)); }
+
+// per-vector warp reduction of a complex FP32 partial -> FP64 in smem slot
+__device__ __forceinline__ void warp_to_smem(float2 acc, double2* slot, int lane) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  if (lane == 0) *slot = make_double2(double(acc.x), double(acc.y));
+}
+
+// dots of the chunk: wp[warp][i] = sum conj(q_i) w  (i < nq), wp[warp][nq] = ||w||^2
+template <class C, int E>
+__device__ __forceinline__ void chunk_dots(const C* const* q, int nq, const C (&wv)[E], long long base, int N,
+                                           int lane, double2* wp) {
+  int i = 0;
+  for (; i + 2 <= nq; i += 2) {
+    const C* q0 = q[i];
+    const C* q1 = q[i + 1];
+    C a0[E], a1[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long idx = base + lane + 32 * e;
+      if (idx < N) { a0[e] = q0[idx]; a1[e] = q1[idx]; } else { a0[e].x = a0[e].y = 0; a1[e].x = a1[e].y = 0; }
+    }
+    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      cfma_conj(s0, to_f2(a0[e]), to_f2(wv[e]));
+      cfma_conj(s1, to_f2(a1[e]), to_f2(wv[e]));
+    }
+    warp_to_smem(s0, wp + i, lane);
+    warp_to_smem(s1, wp + i + 1, lane);
+  }
+  for (; i < nq; ++i) {
+    const C* q0 = q[i];
+    float2 s0 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long idx = base + lane + 32 * e;
+      if (idx < N) cfma_conj(s0, to_f2(q0[idx]), to_f2(wv[e]));
+    }
+    warp_to_smem(s0, wp + i, lane);
+  }
+  float nn = 0.f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) nn += float(wv[e].x) * float(wv[e].x) + float(wv[e].y) * float(wv[e].y);
+  warp_to_smem(make_float2(nn, 0.f), wp + nq, lane);
+}
+
+// FP64 vectors: same, accumulated in FP64 (the FP64 solver path)
+template <int E>
+__device__ __forceinline__ void chunk_dots(const double2* const* q, int nq, const double2 (&wv)[E], long long base,
+                                           int N, int lane, double2* wp) {
+  for (int i = 0; i < nq; ++i) {
+    const double2* q0 = q[i];
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long idx = base + lane + 32 * e;
+      if (idx < N) cfma_conj(s, q0[idx], wv[e]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+    }
+    if (lane == 0) wp[i] = s;
+  }
+  double nn = 0.0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) nn += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
+  if (lane == 0) wp[nq] = make_double2(nn, 0.0);
+}
+
+// CTA partials (sum over warps in FP64) to the global partial array, then the last CTA reduces.
+__device__ void cta_finish(const double2* wp /*[kW][kMaxQ]*/, int nout, double* partial, unsigned* counter,
+                           double2* out, double* wnorm2, int norm_slot) {
+  __syncthreads();
   const int nch = gridDim.x;
-  const int g0 = blockIdx.y * kGroup;
-  T re[kGroup], im[kGroup];
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    double re = 0.0, im = 0.0;
 #pragma unroll
-  for (int i = 0; i < kGroup; ++i) { re[i] = 0; im[i] = 0; }
-  const C* qp[kGroup];
-#pragma unroll
-  for (int i = 0; i < kGroup; ++i) qp[i] = (g0 + i < nq) ? q[g0 + i] : nullptr;
-  const int stride = nch * kThreads;
-  for (int e = blockIdx.x * kThreads + threadIdx.x; e < N; e += stride) {
-    const C wv = w[e];
-#pragma unroll
-    for (int i = 0; i < kGroup; ++i) {
-      const int idx = g0 + i;
-      if (idx < nq) {
-        const C a = qp[i][e];
-        re[i] = fma(a.x, wv.x, re[i]); re[i] = fma(a.y, wv.y, re[i]);
-        im[i] = fma(a.x, wv.y, im[i]); im[i] = fma(-a.y, wv.x, im[i]);
-      } else if (idx == nq) {
-        re[i] = fma(wv.x, wv.x, re[i]); re[i] = fma(wv.y, wv.y, re[i]);
-      }
-    }
+    for (int w = 0; w < kW; ++w) { re += wp[w * kMaxQ + o].x; im += wp[w * kMaxQ + o].y; }
+    partial[(size_t)(2 * o) * nch + blockIdx.x] = re;
+    partial[(size_t)(2 * o + 1) * nch + blockIdx.x] = im;
   }
-  double v[2 * kGroup];
-#pragma unroll
-  for (int i = 0; i < kGroup; ++i) { v[2 * i] = re[i]; v[2 * i + 1] = im[i]; }
-  block_sum<2 * kGroup>(v, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < kGroup; ++i) {
-      const int o = g0 + i;
-      if (o <= nq) {
-        partial[(size_t)(2 * o) * nch + blockIdx.x] = v[2 * i];
-        partial[(size_t)(2 * o + 1) * nch + blockIdx.x] = v[2 * i + 1];
-      }
-    }
-  }
-  if (last_block(counter, gridDim.x * gridDim.y)) {
-    finish(partial, nq + 1, nch, out, wnorm2, nq);
+  if (last_block(counter, gridDim.x)) {
+    finish(partial, nout, nch, out, wnorm2, norm_slot);
     if (threadIdx.x == 0) *counter = 0;
   }
 }
 
-// w = w -/+ sum_i q_i h_i ; optionally ||w||^2 of the result.
-template <class C>
-__global__ void __launch_bounds__(kThreads) k_update(const C* const* q, int nq, const double2* h, int negate, C* w,
-                                                     int N, int with_norm, double* wnorm2, double* partial,
-                                                     unsigned* counter, const int* stop) {
+// h_i = <q_i, w> for i < nq and ||w||^2.
+template <class C, int E>
+__global__ void __launch_bounds__(32 * kW) k_multidot(const C* const* q, int nq, const C* w, int N, double2* out,
+                                                      double* wnorm2, double* partial, unsigned* counter,
+                                                      const int* stop) {
+  if (stop != nullptr && *stop) return;
+  __shared__ double2 wp[kW * kMaxQ];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long base = ((long long)blockIdx.x * kW + warp) * 32 * E;
+  C wv[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const long long idx = base + lane + 32 * e;
+    if (idx < N) wv[e] = w[idx]; else { wv[e].x = 0; wv[e].y = 0; }
+  }
+  chunk_dots(q, nq, wv, base, N, lane, wp + warp * kMaxQ);
+  cta_finish(wp, nq + 1, partial, counter, out, wnorm2, nq);
+}
+
+// w -= sum_i q_i h_i (negate) or += ; then, if with_dots, out = Q^H w and ||w||^2 of the result,
+// else if with_norm only ||w||^2.  One pass over w and two (L2-resident) sweeps of Q's chunk.
+template <class C, int E>
+__global__ void __launch_bounds__(32 * kW) k_update(const C* const* q, int nq, const double2* h, int negate, C* w,
+                                                    int N, int mode /*0: none, 1: norm, 2: dots+norm*/,
+                                                    double2* out, double* wnorm2, double* partial,
+                                                    unsigned* counter, const int* stop) {
   if (stop != nullptr && *stop) return;
   using T = typename Acc<C>::T;
-  extern __shared__ unsigned char smem_raw[];
-  C* hc = reinterpret_cast<C*>(smem_raw);
-  const C** qs = reinterpret_cast<const C**>(smem_raw + sizeof(C) * nq + (16 - (sizeof(C) * nq) % 16) % 16);
-  __shared__ double sh[kThreads / 32 * 2];
-  for (int i = threadIdx.x; i < nq; i += kThreads) {
+  __shared__ double2 wp[kW * kMaxQ];
+  __shared__ C hc[kMaxQ];
+  for (int i = threadIdx.x; i < nq; i += blockDim.x) {
     const double2 v = h[i];
     const double sg = negate ? -1.0 : 1.0;
     hc[i].x = T(sg * v.x);
     hc[i].y = T(sg * v.y);
-    qs[i] = q[i];
   }
   __syncthreads();
-  T nrm = 0;
-  const int stride = gridDim.x * kThreads;
-  for (int e = blockIdx.x * kThreads + threadIdx.x; e < N; e += stride) {
-    C acc = w[e];
-    int i = 0;
-    for (; i + 4 <= nq; i += 4) {
-      const C a0 = qs[i][e], a1 = qs[i + 1][e], a2 = qs[i + 2][e], a3 = qs[i + 3][e];
-      cfma(acc, a0, hc[i]); cfma(acc, a1, hc[i + 1]); cfma(acc, a2, hc[i + 2]); cfma(acc, a3, hc[i + 3]);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long base = ((long long)blockIdx.x * kW + warp) * 32 * E;
+  C wv[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const long long idx = base + lane + 32 * e;
+    if (idx < N) wv[e] = w[idx]; else { wv[e].x = 0; wv[e].y = 0; }
+  }
+  int i = 0;
+  for (; i + 4 <= nq; i += 4) {
+    const C *q0 = q[i], *q1 = q[i + 1], *q2 = q[i + 2], *q3 = q[i + 3];
+    const C h0 = hc[i], h1 = hc[i + 1], h2 = hc[i + 2], h3 = hc[i + 3];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long idx = base + lane + 32 * e;
+      if (idx < N) {
+        const C a0 = q0[idx], a1 = q1[idx], a2 = q2[idx], a3 = q3[idx];
+        cfma(wv[e], a0, h0); cfma(wv[e], a1, h1); cfma(wv[e], a2, h2); cfma(wv[e], a3, h3);
+      }
     }
-    for (; i < nq; ++i) cfma(acc, qs[i][e], hc[i]);
-    w[e] = acc;
-    nrm = fma(acc.x, acc.x, nrm);
-    nrm = fma(acc.y, acc.y, nrm);
   }
-  if (!with_norm) return;
-  double v[2] = {double(nrm), 0.0};
-  block_sum<2>(v, sh);
-  const int nch = gridDim.x;
-  if (threadIdx.x == 0) {
-    partial[blockIdx.x] = v[0];
-    partial[nch + blockIdx.x] = 0.0;
+  for (; i < nq; ++i) {
+    const C* q0 = q[i];
+    const C h0 = hc[i];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long idx = base + lane + 32 * e;
+      if (idx < N) cfma(wv[e], q0[idx], h0);
+    }
   }
-  if (last_block(counter, gridDim.x)) {
-    finish(partial, 1, nch, nullptr, wnorm2, 0);
-    if (threadIdx.x == 0) *counter = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const long long idx = base + lane + 32 * e;
+    if (idx < N) w[idx] = wv[e];
+  }
+  if (mode == 0) return;
+  if (mode == 2) {
+    chunk_dots(q, nq, wv, base, N, lane, wp + warp * kMaxQ);
+    cta_finish(wp, nq + 1, partial, counter, out, wnorm2, nq);
+  } else {
+    chunk_dots(q, 0, wv, base, N, lane, wp + warp * kMaxQ);
+    cta_finish(wp, 1, partial, counter, nullptr, wnorm2, 0);
   }
 }
 
@@ -341,32 +426,58 @@ int elem_grid(int N) {
 
 }  // namespace
 
+namespace {
+int chunk_elems(int N) { return N <= (1 << 18) ? 4 : (N <= (1 << 20) ? 8 : 16); }
+int chunk_grid(int N, int E) { return (int)(((long long)N + 32LL * kW * E - 1) / (32LL * kW * E)); }
+
+template <class C>
+int multidot_t(const void* const* q, int nq, const void* w, int N, double2* out, double* wnorm2, double* partial,
+               unsigned* counter, const int* stop, cudaStream_t s) {
+  const int E = chunk_elems(N);
+  const int grid = chunk_grid(N, E);
+  auto qq = (const C* const*)q;
+  auto ww = (const C*)w;
+  if (E == 4) k_multidot<C, 4><<<grid, 32 * kW, 0, s>>>(qq, nq, ww, N, out, wnorm2, partial, counter, stop);
+  else if (E == 8) k_multidot<C, 8><<<grid, 32 * kW, 0, s>>>(qq, nq, ww, N, out, wnorm2, partial, counter, stop);
+  else k_multidot<C, 16><<<grid, 32 * kW, 0, s>>>(qq, nq, ww, N, out, wnorm2, partial, counter, stop);
+  return grid;
+}
+
+template <class C>
+int update_t(const void* const* q, int nq, const double2* h, int negate, void* w, int N, int mode, double2* out,
+             double* wnorm2, double* partial, unsigned* counter, const int* stop, cudaStream_t s) {
+  const int E = chunk_elems(N);
+  const int grid = chunk_grid(N, E);
+  auto qq = (const C* const*)q;
+  auto ww = (C*)w;
+  if (E == 4)
+    k_update<C, 4><<<grid, 32 * kW, 0, s>>>(qq, nq, h, negate, ww, N, mode, out, wnorm2, partial, counter, stop);
+  else if (E == 8)
+    k_update<C, 8><<<grid, 32 * kW, 0, s>>>(qq, nq, h, negate, ww, N, mode, out, wnorm2, partial, counter, stop);
+  else
+    k_update<C, 16><<<grid, 32 * kW, 0, s>>>(qq, nq, h, negate, ww, N, mode, out, wnorm2, partial, counter, stop);
+  return grid;
+}
+}  // namespace
+
+int max_reduction_chunks(int N) { return chunk_grid(N, chunk_elems(N)); }
+
 int launch_multidot(int prec64, const void* const* q, int nq, const void* w, int N, double2* out, double* wnorm2,
                     double* partial, unsigned* counter, const int* stop, cudaStream_t s) {
-  const dim3 grid(chunks_for(N), (nq + 1 + kGroup - 1) / kGroup);
-  if (prec64)
-    k_multidot<double2><<<grid, kThreads, 0, s>>>((const double2* const*)q, nq, (const double2*)w, N, out, wnorm2,
-                                                  partial, counter, stop);
-  else
-    k_multidot<float2><<<grid, kThreads, 0, s>>>((const float2* const*)q, nq, (const float2*)w, N, out, wnorm2,
-                                                 partial, counter, stop);
+  if (nq + 1 > kMaxQ) { set_error("multi-dot of %d vectors exceeds %d", nq, kMaxQ - 1); return COARSE_ERR_INVALID_ARG; }
+  if (prec64) multidot_t<double2>(q, nq, w, N, out, wnorm2, partial, counter, stop, s);
+  else multidot_t<float2>(q, nq, w, N, out, wnorm2, partial, counter, stop, s);
   note_launch();
   COARSE_CUDA(cudaGetLastError());
   return COARSE_OK;
 }
 
 int launch_update(int prec64, const void* const* q, int nq, const double2* h, int negate, void* w, int N,
-                  int with_dot, double2* /*out_dots*/, double* wnorm2, double* partial, unsigned* counter,
+                  int mode, double2* out_dots, double* wnorm2, double* partial, unsigned* counter,
                   const int* stop, cudaStream_t s) {
-  const int grid = chunks_for(N);
-  const size_t csz = prec64 ? sizeof(double2) : sizeof(float2);
-  const size_t smem = csz * nq + 16 + sizeof(void*) * nq;
-  if (prec64)
-    k_update<double2><<<grid, kThreads, smem, s>>>((const double2* const*)q, nq, h, negate, (double2*)w, N, with_dot,
-                                                   wnorm2, partial, counter, stop);
-  else
-    k_update<float2><<<grid, kThreads, smem, s>>>((const float2* const*)q, nq, h, negate, (float2*)w, N, with_dot,
-                                                  wnorm2, partial, counter, stop);
+  if (nq + 1 > kMaxQ) { set_error("update with %d vectors exceeds %d", nq, kMaxQ - 1); return COARSE_ERR_INVALID_ARG; }
+  if (prec64) update_t<double2>(q, nq, h, negate, w, N, mode, out_dots, wnorm2, partial, counter, stop, s);
+  else update_t<float2>(q, nq, h, negate, w, N, mode, out_dots, wnorm2, partial, counter, stop, s);
   note_launch();
   COARSE_CUDA(cudaGetLastError());
   return COARSE_OK;

@@ -151,9 +151,12 @@ template <class C> struct VecList { const C* const* v; int count; };
 
 int launch_multidot(int prec64, const void* const* q, int nq, const void* w, int N, double2* out,
                     double* wnorm2, double* partial, unsigned* counter, const int* stop, cudaStream_t s);
+// w -= (negate) / += sum_i q_i h_i; mode 0: nothing else, 1: ||w||^2 -> wnorm2, 2: out = Q^H w and
+// ||w||^2 of the updated w (fused second Gram-Schmidt pass).
 int launch_update(int prec64, const void* const* q, int nq, const double2* h, int negate, void* w, int N,
-                  int with_dot, double2* out_dots, double* wnorm2, double* partial, unsigned* counter,
+                  int mode, double2* out_dots, double* wnorm2, double* partial, unsigned* counter,
                   const int* stop, cudaStream_t s);
+int max_reduction_chunks(int N);  // partial-array columns the reductions use for length N
 int launch_combine(int prec64, const void* const* in, int nin, const double2* coef, int ldc, void* const* out,
                    int nout, int accumulate, int N, const int* stop, cudaStream_t s);
 int launch_scale(int prec64, const void* x, const double* inv_or_null, double2 alpha, void* y, int N,

@@ -38,77 +38,112 @@ __global__ void k_cycle_init(CycleState* st, int k, int steps, const double* rno
   }
 }
 
-__global__ void k_step_finalize(CycleState* st, const double2* h1, const double2* h2, Dense d) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (st->stop) return;
+// One warp.  Loads and stores are lane-parallel; only the j rotations of the new
+// column (inherently sequential) and the new rotation run on lane 0.
+__global__ void __launch_bounds__(32) k_step_finalize(CycleState* st, const double2* h1, const double2* h2, Dense d) {
+  __shared__ double2 col[kMaxDense + 2];
+  __shared__ double csh[kMaxDense];
+  __shared__ double2 snh[kMaxDense];
+  __shared__ double hn2s;
+  const int lane = threadIdx.x;
+  if (st->stop) return;  // every lane reads the same flag
   const int j = st->j, k = st->k, ldh = d.ldh;
   double hn2 = 0.0;
-  for (int i = 0; i < k; ++i) {
+  for (int i = lane; i < k; i += 32) {
     const double2 b = add(h1[i], h2[i]);
     d.B[j * d.ldb + i] = b;
     hn2 += abs2(b);
   }
-  for (int i = 0; i <= j; ++i) {
+  for (int i = lane; i <= j; i += 32) {
     const double2 h = add(h1[k + i], h2[k + i]);
     d.H[j * ldh + i] = h;
-    d.R[j * ldh + i] = h;
+    col[i] = h;
     hn2 += abs2(h);
   }
-  const double wn2 = fmax(st->wnorm2, 0.0);
-  const double hj1 = sqrt(wn2);
-  hn2 += wn2;
-  d.H[j * ldh + j + 1] = make_double2(hj1, 0.0);
-  d.R[j * ldh + j + 1] = make_double2(hj1, 0.0);
-  for (int i = 0; i < j; ++i) {
-    const double2 u = d.R[j * ldh + i], w = d.R[j * ldh + i + 1];
-    d.R[j * ldh + i] = add(scal(u, d.cs[i]), mul(d.sn[i], w));
-    d.R[j * ldh + i + 1] = sub(scal(w, d.cs[i]), conjmul(d.sn[i], u));
+  for (int i = lane; i < j; i += 32) {
+    csh[i] = d.cs[i];
+    snh[i] = d.sn[i];
   }
-  double c;
-  double2 s, r;
-  givens(d.R[j * ldh + j], d.R[j * ldh + j + 1], c, s, r);
-  d.cs[j] = c;
-  d.sn[j] = s;
-  d.R[j * ldh + j] = r;
-  d.R[j * ldh + j + 1] = make_double2(0.0, 0.0);
-  const double2 gj = d.g[j];
-  d.g[j] = scal(gj, c);
-  d.g[j + 1] = scal(conjmul(s, gj), -1.0);
-  const double resid = cabs(d.g[j + 1]);
-  st->j = j + 1;
-  st->resid = resid;
-  st->inv_h = hj1 > 0.0 ? 1.0 / hj1 : 0.0;
-  if (!isfinite(hn2) || !isfinite(resid)) {
-    st->stop = 1;
-    st->status |= ST_NONFINITE;
-    return;
+  for (int off = 16; off > 0; off >>= 1) hn2 += __shfl_xor_sync(0xffffffffu, hn2, off);
+  __syncwarp();
+  if (lane == 0) {
+    const double wn2 = fmax(st->wnorm2, 0.0);
+    const double hj1 = sqrt(wn2);
+    hn2 += wn2;
+    hn2s = hn2;
+    d.H[j * ldh + j + 1] = make_double2(hj1, 0.0);
+    col[j + 1] = make_double2(hj1, 0.0);
+    for (int i = 0; i < j; ++i) {
+      const double2 u = col[i], w = col[i + 1];
+      col[i] = add(scal(u, csh[i]), mul(snh[i], w));
+      col[i + 1] = sub(scal(w, csh[i]), conjmul(snh[i], u));
+    }
+    double c;
+    double2 sg, r;
+    givens(col[j], col[j + 1], c, sg, r);
+    d.cs[j] = c;
+    d.sn[j] = sg;
+    col[j] = r;
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 gj = d.g[j];
+    d.g[j] = scal(gj, c);
+    d.g[j + 1] = scal(conjmul(sg, gj), -1.0);
+    const double resid = cabs(d.g[j + 1]);
+    st->resid = resid;
+    st->inv_h = hj1 > 0.0 ? 1.0 / hj1 : 0.0;
+    int stop = 0, status = st->status;
+    if (!isfinite(hn2) || !isfinite(resid)) {
+      stop = 1;
+      status |= ST_NONFINITE;
+    } else {
+      if (resid <= st->target) stop = 1;
+      if (hj1 <= 1e-14 * sqrt(hn2)) {  // invariant Krylov space: the least-squares solution is exact
+        stop = 1;
+        status |= ST_LUCKY;
+      }
+      if (j + 1 >= st->steps) stop = 1;
+    }
+    st->status = status;
+    st->stop = stop;
   }
-  if (resid <= st->target) st->stop = 1;
-  if (hj1 <= 1e-14 * sqrt(hn2)) {  // invariant Krylov space: the least-squares solution is exact
-    st->stop = 1;
-    st->status |= ST_LUCKY;
-  }
-  if (j + 1 >= st->steps) st->stop = 1;
+  __syncwarp();
+  for (int i = lane; i <= j + 1; i += 32) d.R[j * ldh + i] = col[i];
+  __syncwarp();
+  if (lane == 0) st->j = j + 1;  // last: the normalisation kernel of this step keys on st->j == j + 1
 }
 
-__global__ void k_cycle_solve(const CycleState* st, Dense d) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One warp: y = R^{-1} g by column-oriented back substitution (R staged in shared memory,
+// lane r owns right-hand-side rows r and r + 32), then y_U = -B y_V and z = Hbar y_V.
+__global__ void __launch_bounds__(32) k_cycle_solve(const CycleState* st, Dense d) {
+  extern __shared__ double2 Rs[];  // kMaxDense columns of d.ldh entries
+  __shared__ double2 ys[kMaxDense];
+  const int lane = threadIdx.x;
   const int j = st->j, k = st->k, ldh = d.ldh;
-  double2* y = d.ycoef + k;  // y_V
+  for (int e = lane; e < j * ldh; e += 32) Rs[e] = d.R[e];
+  double2 x0 = lane < j ? d.g[lane] : make_double2(0.0, 0.0);
+  double2 x1 = lane + 32 < j ? d.g[lane + 32] : make_double2(0.0, 0.0);
+  __syncwarp();
   for (int i = j - 1; i >= 0; --i) {
-    double2 s = d.g[i];
-    for (int l = i + 1; l < j; ++l) s = sub(s, mul(d.R[l * ldh + i], y[l]));
-    const double2 piv = d.R[i * ldh + i];
-    y[i] = cabs(piv) > kSafeMin ? cdiv(s, piv) : make_double2(0.0, 0.0);
+    const double2 xi_lo = make_double2(__shfl_sync(0xffffffffu, x0.x, i & 31), __shfl_sync(0xffffffffu, x0.y, i & 31));
+    const double2 xi_hi = make_double2(__shfl_sync(0xffffffffu, x1.x, i & 31), __shfl_sync(0xffffffffu, x1.y, i & 31));
+    const double2 xi = i < 32 ? xi_lo : xi_hi;
+    const double2 piv = Rs[i * ldh + i];
+    const double2 yi = cabs(piv) > kSafeMin ? cdiv(xi, piv) : make_double2(0.0, 0.0);
+    if (lane == 0) ys[i] = yi;
+    if (lane < i) x0 = sub(x0, mul(Rs[i * ldh + lane], yi));
+    if (lane + 32 < i) x1 = sub(x1, mul(Rs[i * ldh + lane + 32], yi));
   }
-  for (int i = 0; i < k; ++i) {
+  __syncwarp();
+  double2* y = d.ycoef + k;  // y_V
+  for (int i = lane; i < j; i += 32) y[i] = ys[i];
+  for (int i = lane; i < k; i += 32) {
     double2 s = make_double2(0.0, 0.0);
-    for (int l = 0; l < j; ++l) s = add(s, mul(d.B[l * d.ldb + i], y[l]));
+    for (int l = 0; l < j; ++l) s = add(s, mul(d.B[l * d.ldb + i], ys[l]));
     d.ycoef[i] = scal(s, -1.0);
   }
-  for (int i = 0; i <= j; ++i) {
+  for (int i = lane; i <= j; i += 32) {
     double2 s = make_double2(0.0, 0.0);
-    for (int l = (i > 0 ? i - 1 : 0); l < j; ++l) s = add(s, mul(d.H[l * ldh + i], y[l]));
+    for (int l = (i > 0 ? i - 1 : 0); l < j; ++l) s = add(s, mul(d.H[l * ldh + i], ys[l]));
     d.z[i] = s;
   }
 }
@@ -310,7 +345,13 @@ int launch_step_finalize(CycleState* st, const double2* h1, const double2* h2, c
 }
 
 int launch_cycle_solve(const CycleState* st, const Dense& d, cudaStream_t s) {
-  k_cycle_solve<<<1, 32, 0, s>>>(st, d);
+  static bool attr = false;
+  const size_t smem = sizeof(double2) * (size_t)kMaxDense * d.ldh;
+  if (!attr) {
+    COARSE_CUDA(cudaFuncSetAttribute(k_cycle_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  k_cycle_solve<<<1, 32, smem, s>>>(st, d);
   note_launch();
   COARSE_CUDA(cudaGetLastError());
   return COARSE_OK;

@@ -95,7 +95,8 @@ int Solver::ensure(int m, int k, int dmax) {
   const size_t o_cs = cnt(kMaxDense), o_sn = cnt(kMaxDense), o_g = cnt(kMaxDense + 1), o_B = cnt((size_t)kMaxK * kMaxDense);
   const size_t o_y = cnt(maxq), o_z = cnt(maxq), o_cC = cnt((size_t)maxq * kMaxK), o_cU = cnt((size_t)maxq * kMaxK);
   const size_t o_th = cnt(kMaxPoly + 1), o_pc = cnt(kPolyScale + 1), o_SW = cnt((size_t)kMaxK * maxq);
-  const size_t o_part = cnt((size_t)(2 * maxq + 4) * 304), o_st = cnt(sizeof(CycleState) / sizeof(double2) + 1);
+  const int nch = max_reduction_chunks(N) > 304 ? max_reduction_chunks(N) : 304;
+  const size_t o_part = cnt((size_t)(maxq + 8) * nch), o_st = cnt(sizeof(CycleState) / sizeof(double2) + 1);
   const size_t o_n2 = cnt(8), o_cnt = cnt(4), o_tab = cnt(16 * (size_t)(2 * maxq + 8));
   TRY(dalloc((char**)&smallmem, nsmall));
   char* b = (char*)smallmem;
@@ -221,9 +222,9 @@ int Solver::arnoldi_step(int j, int kc, void* const* tab) {
   const int* stop = &st->stop;
   const int nq = kc + j + 1;
   void* wv = V[j + 1];
+  // pass 1: h1 = Q^H w;  w -= Q h1 fused with pass 2's dots h2 = Q^H w;  w -= Q h2 with ||w||^2
   TRY(launch_multidot(v64, (const void* const*)tab, nq, wv, N, h1, nullptr, partial, counter, stop, stream));
-  TRY(launch_update(v64, (const void* const*)tab, nq, h1, 1, wv, N, 0, nullptr, nullptr, partial, counter, stop, stream));
-  TRY(launch_multidot(v64, (const void* const*)tab, nq, wv, N, h2, nullptr, partial, counter, stop, stream));
+  TRY(launch_update(v64, (const void* const*)tab, nq, h1, 1, wv, N, 2, h2, nullptr, partial, counter, stop, stream));
   TRY(launch_update(v64, (const void* const*)tab, nq, h2, 1, wv, N, 1, nullptr, &st->wnorm2, partial, counter, stop,
                     stream));
   TRY(launch_step_finalize(st, h1, h2, dn, stream));
