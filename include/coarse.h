@@ -120,6 +120,27 @@ int coarse_apply_adjoint(const coarse_op* op, const void* x, void* y, int nrhs, 
 int coarse_residual(const coarse_op* op, const void* b, const void* x, void* r, double* norms_host,
                     void* stream);
 
+/*
+ * coarse_residual_noalloc -- the same result as coarse_residual (r = b - D_c x in
+ * FP64, and ||r||, ||b|| into norms_host[2]), for callers that cannot allocate
+ * device memory during the call: a runtime whose device memory is owned by an
+ * outside pool or arena, or a code path where allocating would block or is not
+ * permitted.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ * Instead of the operator's own work memory, all of its scratch (stencil pulls,
+ * pushes and arrival counters, reduction partials) lives in one static device
+ * array of about 10.5 MB that every device loading the library holds until exit.
+ * The paper has no counterpart of this call.
+ * Limit: V*n <= 131072 unknowns; larger operators get COARSE_ERR_INVALID_ARG.
+ * The array is looked up once per device (cudaGetSymbolAddress) on the first
+ * call made with that device current; make that first call before any stream
+ * capture.  Every call shares the array, which keeps the previous call's
+ * contents (the counters that must start at zero are cleared at the start of
+ * each call): calls that overlap on the GPU, from any stream or thread, race and
+ * must not be issued.  Synchronises `stream`.
+ */
+int coarse_residual_noalloc(const coarse_op* op, const void* b, const void* x, void* r, double* norms_host,
+                            void* stream);
+
 /* Flags of coarse_solve_params.flags */
 #define COARSE_ZERO_GUESS 0x1u      /* ignore the incoming x, start from 0 */
 #define COARSE_REBUILD_POLY 0x2u    /* recompute the polynomial before this solve */

@@ -20,7 +20,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED"
 # every symbol the header declares
 EXPORTS = ["coarse_op_create", "coarse_op_update", "coarse_op_destroy", "coarse_apply", "coarse_apply_adjoint",
            "coarse_residual", "coarse_solve", "coarse_solve_adjoint", "coarse_solve_batched", "coarse_block_grad",
-           "coarse_op_poly", "coarse_last_error", "coarse_version"]
+           "coarse_op_poly", "coarse_last_error", "coarse_version", "coarse_residual_noalloc"]
 
 
 class CoarseError(RuntimeError):
@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
     L.coarse_apply.argtypes = [vp, vp, vp, i32, i32, vp]
     L.coarse_apply_adjoint.argtypes = [vp, vp, vp, i32, i32, vp]
     L.coarse_residual.argtypes = [vp, vp, vp, vp, P(dbl), vp]
+    L.coarse_residual_noalloc.argtypes = [vp, vp, vp, vp, P(dbl), vp]
     L.coarse_solve.argtypes = [vp, vp, vp, i32, P(SolveParams), P(SolveInfo), vp]
     L.coarse_solve_adjoint.argtypes = [vp, vp, vp, i32, P(SolveParams), P(SolveInfo), vp]
     L.coarse_solve_batched.argtypes = [P(vp), i32, P(vp), P(vp), P(i32), P(SolveParams), P(SolveInfo), vp]
