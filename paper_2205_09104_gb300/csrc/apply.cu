@@ -15,265 +15,20 @@
 //   transposed   y'_j += conj(F_ij) w'_i : CPL column sums per lane, reduced over g
 // without shared-memory staging of the block.
 #include "common.cuh"
+#include "apply_core.cuh"
+#include "batch.cuh"
 
 namespace coarse {
 namespace {
 
-// BF16 complex (re, im) in 32 bits -> float2
-__device__ __forceinline__ float2 bf2f(uint32_t u) {
-  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
-}
-
-template <class VT, class AC, int CPL>
-__device__ __forceinline__ void load_vec(const VT* p, AC (&w)[CPL]) {
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) { VT v = p[c]; w[c].x = v.x; w[c].y = v.y; }
-}
-template <class VT, class AC, int CPL>
-__device__ __forceinline__ void store_vec(VT* p, const AC (&w)[CPL]) {
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) { VT v; v.x = w[c].x; v.y = w[c].y; p[c] = v; }
-}
-
-// Streaming (read-once) block loads: evict-first so that the per-site pushes stay in L2.
-template <class T> __device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
-
-template <class AC, class BT> struct LoadS;
-template <> struct LoadS<double2, double2> {
-  template <int CPL> __device__ __forceinline__ static void row(const double2* p, double2 (&e)[CPL]) {
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) e[c] = ld_stream(p + c);
-  }
-};
-template <> struct LoadS<float2, float2> {
-  template <int CPL> __device__ __forceinline__ static void row(const float2* p, float2 (&e)[CPL]) {
-    const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-    for (int c = 0; c < CPL / 2; ++c) {
-      float4 v = ld_stream(q + c);
-      e[2 * c] = make_float2(v.x, v.y);
-      e[2 * c + 1] = make_float2(v.z, v.w);
-    }
-  }
-};
-template <> struct LoadS<float2, cbf16> {
-  template <int CPL> __device__ __forceinline__ static void row(const cbf16* p, float2 (&e)[CPL]) {
-    if constexpr ((CPL * 4) % 16 == 0) {
-      const uint4* q = reinterpret_cast<const uint4*>(p);
-#pragma unroll
-      for (int c = 0; c < CPL / 4; ++c) {
-        uint4 v = ld_stream(q + c);
-        e[4 * c] = bf2f(v.x); e[4 * c + 1] = bf2f(v.y); e[4 * c + 2] = bf2f(v.z); e[4 * c + 3] = bf2f(v.w);
-      }
-    } else {
-      const uint2* q = reinterpret_cast<const uint2*>(p);
-#pragma unroll
-      for (int c = 0; c < CPL / 2; ++c) {
-        uint2 v = ld_stream(q + c);
-        e[2 * c] = bf2f(v.x); e[2 * c + 1] = bf2f(v.y);
-      }
-    }
-  }
-};
-
-template <class AC> __device__ __forceinline__ AC ld_cg(const AC* p);
-template <> __device__ __forceinline__ float2 ld_cg<float2>(const float2* p) { return __ldcg(p); }
-template <> __device__ __forceinline__ double2 ld_cg<double2>(const double2* p) { return __ldcg(p); }
-
-// Finish the sites flagged in `fin` (bit 0: `site`, bit 1+mu: its forward neighbour mu):
-//   y_z = P_z + T_0[z-0] + T_1[z-1] + T_2[z-2] + T_3[z-3] + i mu sigma3 v_z, then the epilogue.
-// Called by the 8 lanes of row group 0 (lane t owns columns t*CPL ...).
-template <int N, class VT, class AC>
-__device__ __forceinline__ void finish_sites(const ApplyArgs& a, int site, int fin, int t,
-                                             decltype(AC{}.x) st, const AC* Pb, const AC* Tb) {
-  constexpr int CPL = N / 8;
-  using AT = decltype(AC{}.x);
-  const int V = a.V;
-  const double2 c0d = a.mode != APPLY_PLAIN ? a.coef[0] : make_double2(0.0, 0.0);
-  const double2 c1d = a.mode != APPLY_PLAIN ? a.coef[1] : make_double2(0.0, 0.0);
-  const double2 c2d = a.mode == APPLY_POLY_FIRST ? a.coef[2] : make_double2(0.0, 0.0);
-  const AC c0{AT(c0d.x), AT(c0d.y)}, c1{AT(c1d.x), AT(c1d.y)}, c2{AT(c2d.x), AT(c2d.y)};
-  const VT* X = static_cast<const VT*>(a.x);
-#pragma unroll 1
-  for (int q = 0; q < 5; ++q) {
-    if (!(fin & (1 << q))) continue;
-    const int z = q == 0 ? site : __ldg(a.nb + site * 8 + (q - 1));
-    AC r[CPL], xs[CPL];
-    load_vec<VT, AC, CPL>(X + (size_t)z * N + t * CPL, xs);
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) r[c] = ld_cg(Pb + (size_t)z * N + t * CPL + c);
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      const int from = __ldg(a.nb + z * 8 + 4 + mu);
-      const AC* srcp = Tb + ((size_t)mu * V + from) * N + t * CPL;
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) r[c] = cadd(r[c], ld_cg(srcp + c));
-    }
-    const AT m = AT(a.mu) * st;  // + i mu sigma3 v
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      r[c].x -= m * xs[c].y;
-      r[c].y += m * xs[c].x;
-    }
-    VT* Y = static_cast<VT*>(a.y) + (size_t)z * N + t * CPL;
-    if (a.mode == APPLY_PLAIN) {
-      store_vec<VT, AC, CPL>(Y, r);
-    } else if (a.mode == APPLY_AXPBY) {
-      AC zz[CPL];
-      load_vec<VT, AC, CPL>(static_cast<const VT*>(a.z) + (size_t)z * N + t * CPL, zz);
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) r[c] = cadd(cmul(c0, r[c]), cmul(c1, zz[c]));
-      store_vec<VT, AC, CPL>(Y, r);
-    } else {
-      // polynomial chain: s' = s - c0 * D s ; acc = acc + c1 * s'  (first step: acc = c2 * s + c1 * s')
-      VT* Acc = static_cast<VT*>(a.acc) + (size_t)z * N + t * CPL;
-      AC ac[CPL];
-      if (a.mode == APPLY_POLY_FIRST) {
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) ac[c] = cmul(c2, xs[c]);
-      } else {
-        load_vec<VT, AC, CPL>(Acc, ac);
-      }
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        r[c] = csub(xs[c], cmul(c0, r[c]));
-        ac[c] = cadd(ac[c], cmul(c1, r[c]));
-      }
-      store_vec<VT, AC, CPL>(Y, r);
-      store_vec<VT, AC, CPL>(Acc, ac);
-    }
-    if (t == 0) a.cnt[z] = 0;
-  }
-}
-
-// Push-pull apply.  The warp of site x reads its 5 stored blocks once:
-//   pull  P_x      = A_x v_x + sum_mu F_{x,mu} v_{x+mu}            (row sums)
-//   push  T_mu[x]  = sigma3 F_{x,mu}^H sigma3 v_x                  (column sums, for site x+mu)
-// and writes them to scratch.  Each site receives 5 contributions (its own
-// pull and one push per direction from x-mu); a per-site counter tells the
-// warp that delivers the 5th contribution to finish the site:
-//   y_z = P_z + T_0[z-0] + T_1[z-1] + T_2[z-2] + T_3[z-3] + i mu sigma3 v_z, then the epilogue.
-// The sum order is fixed, so results do not depend on which warp finishes.
-// The finisher resets the counter to 0 for the next launch.  No thread ever
-// waits for another.
 template <int N, class BT, class VT, class AC>
 __global__ void __launch_bounds__(128) k_apply(ApplyArgs a) {
-  constexpr int CPL = N / 8, KR = N / 4, NV = N / 2;
-  using AT = decltype(AC{}.x);
   if (a.stop != nullptr && *a.stop) return;
   __shared__ AC ys[4][N];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int site = blockIdx.x * 4 + warp;
   if (site >= a.V) return;  // warp-uniform
-  const int g = lane >> 3, t = lane & 7;
-  const int V = a.V;
-  const BT* B = static_cast<const BT*>(a.blocks);
-  const VT* X = static_cast<const VT*>(a.x);
-  AC* Pb = static_cast<AC*>(a.part);
-  AC* Tb = static_cast<AC*>(a.push);
-  constexpr size_t BSZ = (size_t)N * N;
-  const AT st = (t * CPL < NV) ? AT(1) : AT(-1);  // sigma3 of this lane's columns
-  const int adj = a.adjoint;
-
-  // own vector: the lane's columns (pull of the self block) and its rows (pushes)
-  AC w0[CPL], xr[KR];
-  load_vec<VT, AC, CPL>(X + (size_t)site * N + t * CPL, w0);
-#pragma unroll
-  for (int k = 0; k < KR; ++k) {
-    const VT v = X[(size_t)site * N + 4 * k + g];
-    const AT sk = (adj || 4 * k + g < NV) ? AT(1) : AT(-1);  // sigma3 on the push input
-    xr[k].x = sk * AT(v.x);
-    xr[k].y = sk * AT(v.y);
-  }
-  AC yf[KR];
-#pragma unroll
-  for (int k = 0; k < KR; ++k) yf[k] = AC{0, 0};
-  {
-    AC w[CPL];
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) w[c] = adj ? cscale(w0[c], st) : w0[c];
-    const BT* blk = B + (size_t)site * 5 * BSZ + g * N + t * CPL;
-#pragma unroll
-    for (int k = 0; k < KR; ++k) {
-      AC e[CPL];
-      LoadS<AC, BT>::template row<CPL>(blk + (size_t)k * 4 * N, e);
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) cfma(yf[k], e[c], w[c]);
-    }
-  }
-  const AT so = adj ? AT(1) : st;  // sigma3 on the push output (columns)
-#pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {
-    const int src = __ldg(a.nb + site * 8 + mu);
-    AC w[CPL];
-    load_vec<VT, AC, CPL>(X + (size_t)src * N + t * CPL, w);
-    if (adj) {
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) w[c] = cscale(w[c], st);
-    }
-    AC yb[CPL];
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) yb[c] = AC{0, 0};
-    const BT* blk = B + ((size_t)site * 5 + 1 + mu) * BSZ + g * N + t * CPL;
-#pragma unroll
-    for (int k = 0; k < KR; ++k) {
-      AC e[CPL];
-      LoadS<AC, BT>::template row<CPL>(blk + (size_t)k * 4 * N, e);
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        cfma(yf[k], e[c], w[c]);
-        cfma_conj(yb[c], e[c], xr[k]);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-#pragma unroll
-      for (int off = 8; off < 32; off <<= 1) {
-        yb[c].x += __shfl_xor_sync(0xffffffffu, yb[c].x, off);
-        yb[c].y += __shfl_xor_sync(0xffffffffu, yb[c].y, off);
-      }
-    }
-    if (g == 0) {
-      AC* dst = Tb + ((size_t)mu * V + site) * N + t * CPL;
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) dst[c] = cscale(yb[c], so);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < KR; ++k) {
-#pragma unroll
-    for (int off = 1; off < 8; off <<= 1) {
-      yf[k].x += __shfl_xor_sync(0xffffffffu, yf[k].x, off);
-      yf[k].y += __shfl_xor_sync(0xffffffffu, yf[k].y, off);
-    }
-  }
-  if (t == 0) {
-#pragma unroll
-    for (int k = 0; k < KR; ++k) {
-      const AT sr = (adj && 4 * k + g >= NV) ? AT(-1) : AT(1);
-      ys[warp][4 * k + g] = cscale(yf[k], sr);
-    }
-  }
-  __syncwarp();
-  if (g == 0) {
-    AC* dst = Pb + (size_t)site * N + t * CPL;
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) dst[c] = ys[warp][t * CPL + c];
-  }
-  // publish: every lane fences its own stores, then lane 0 counts the 5 deliveries
-  __threadfence();
-  __syncwarp();
-  int fin = 0;
-  if (lane == 0) {
-    if (atomicAdd(a.cnt + site, 1) == 4) fin |= 1;
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu)
-      if (atomicAdd(a.cnt + __ldg(a.nb + site * 8 + mu), 1) == 4) fin |= 2 << mu;
-  }
-  fin = __shfl_sync(0xffffffffu, fin, 0);
-  if (fin == 0 || g != 0) return;
-  __threadfence();
-  finish_sites<N, VT, AC>(a, site, fin, t, st, Pb, Tb);
+  apply_site<N, BT, VT, AC>(a, site, ys[warp]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -415,10 +170,16 @@ __global__ void __launch_bounds__(32 * TmaCfg<N, BT>::kWarps, 1) k_apply_tma(App
   bool ok = true;
   int it = 0;
   for (int site = s0; site < s1; ++site) {
-    AC xr[KR];
-    AC yf[KR];
+    // Packed FP32x2 accumulation: with e = (re, im) of a block entry used as-is,
+    //   forward   yf += e*w      : F1 += e (.) (w.x, w.x),  F2 += e (.) (w.y, w.y)
+    //             -> yf = (F1.x - F2.y, F2.x + F1.y)
+    //   transpose yb += conj(e)*x : B1 += e (.) (x.x, x.x),  B2 += e (.) (x.y, x.y)
+    //             -> yb = (B1.x + B2.y, B2.x - B1.y)
+    // so each entry costs four __ffma2_rn and no operand shuffling.
+    float2 xr1[KR], xr2[KR];
+    float2 F1[KR], F2[KR];
 #pragma unroll
-    for (int k = 0; k < KR; ++k) yf[k] = AC{0, 0};
+    for (int k = 0; k < KR; ++k) { F1[k] = make_float2(0.f, 0.f); F2[k] = make_float2(0.f, 0.f); }
     const AT so = adj ? AT(1) : st;
 #pragma unroll 1
     for (int b = 0; b < 5; ++b, ++it) {
@@ -426,36 +187,45 @@ __global__ void __launch_bounds__(32 * TmaCfg<N, BT>::kWarps, 1) k_apply_tma(App
       if (!mbar_wait(bar + sidx, (uint32_t)((it / S) & 1))) ok = false;
       if (!__all_sync(0xffffffffu, ok)) break;
       const VT* vs = reinterpret_cast<const VT*>(stage0 + (size_t)sidx * SB + BB);
-      AC w[CPL];
-      load_vec<VT, AC, CPL>(vs + t * CPL, w);
+      float2 w1[CPL], w2[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const VT v = vs[t * CPL + c];
+        const AT sc = adj ? st : AT(1);
+        w1[c] = make_float2(sc * v.x, sc * v.x);
+        w2[c] = make_float2(sc * v.y, sc * v.y);
+      }
       if (b == 0) {
         // own vector: its rows feed the pushes of the four hop blocks
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
           const VT v = vs[4 * k + g];
           const AT sk = (adj || 4 * k + g < NV) ? AT(1) : AT(-1);
-          xr[k].x = sk * v.x;
-          xr[k].y = sk * v.y;
+          xr1[k] = make_float2(sk * v.x, sk * v.x);
+          xr2[k] = make_float2(sk * v.y, sk * v.y);
         }
       }
-      if (adj) {
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) w[c] = cscale(w[c], st);
-      }
       const BT* blk = reinterpret_cast<const BT*>(stage0 + (size_t)sidx * SB) + g * N + t * CPL;
-      AC yb[CPL];
+      float2 B1[CPL], B2[CPL];
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) yb[c] = AC{0, 0};
+      for (int c = 0; c < CPL; ++c) { B1[c] = make_float2(0.f, 0.f); B2[c] = make_float2(0.f, 0.f); }
 #pragma unroll
       for (int k = 0; k < KR; ++k) {
         AC e[CPL];
         SmemRow<BT>::template row<CPL>(blk + (size_t)k * 4 * N, e);
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-          cfma(yf[k], e[c], w[c]);
-          if (b > 0) cfma_conj(yb[c], e[c], xr[k]);
+          F1[k] = __ffma2_rn(e[c], w1[c], F1[k]);
+          F2[k] = __ffma2_rn(e[c], w2[c], F2[k]);
+          if (b > 0) {
+            B1[c] = __ffma2_rn(e[c], xr1[k], B1[c]);
+            B2[c] = __ffma2_rn(e[c], xr2[k], B2[c]);
+          }
         }
       }
+      AC yb[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) yb[c] = make_float2(B1[c].x + B2[c].y, B2[c].x - B1[c].y);
       __syncwarp();  // every lane has finished reading this stage
       if (lane == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -478,8 +248,10 @@ __global__ void __launch_bounds__(32 * TmaCfg<N, BT>::kWarps, 1) k_apply_tma(App
       }
     }
     if (!__all_sync(0xffffffffu, ok)) break;
+    AC yf[KR];
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
+      yf[k] = make_float2(F1[k].x - F2[k].y, F2[k].x + F1[k].y);
 #pragma unroll
       for (int off = 1; off < 8; off <<= 1) {
         yf[k].x += __shfl_xor_sync(0xffffffffu, yf[k].x, off);
@@ -578,6 +350,70 @@ int launch_tma(int n, const ApplyArgs& a, cudaStream_t s) {
   return COARSE_ERR_INVALID_ARG;
 }
 
+// ------------------------------------------------------------------------------------------
+// Batched stencil: one launch applies D_c for every solve of an n-group.  Warp g of the flat
+// grid takes global site g, finds its solve through the site prefix sums and runs the same
+// per-site push-pull body as k_apply with that solve's operator, vectors and scratch.
+template <int N, class BT>
+__global__ void __launch_bounds__(128) kb_apply(BApply b) {
+  __shared__ float2 ys[4][N];
+  const int warp = threadIdx.x >> 5;
+  const int g = blockIdx.x * 4 + warp;
+  if (g >= b.total) return;
+  const int k = find_solve(b.site_off, b.count, g);
+  const BSolve& s = b.S[b.sidx[k]];
+  if (!bgate(s, b.gate)) return;  // uniform for all sites of the solve
+  const int step = *b.step;
+  ApplyArgs a;
+  a.blocks = s.blk;
+  a.nb = s.nb;
+  a.V = s.V;
+  a.mu = s.mu;
+  a.x = bsel(s, b.xsel, step);
+  a.y = bsel(s, b.ysel, step);
+  a.z = nullptr;
+  a.acc = s.acc;
+  a.coef = s.polyc + b.coef_off;
+  a.mode = b.mode;
+  a.adjoint = 0;
+  a.stop = nullptr;
+  a.part = s.part;
+  a.push = s.push;
+  a.cnt = s.cnt;
+  a.err = s.cnt + s.V;
+  apply_site<N, BT, float2, float2>(a, g - b.site_off[k], ys[warp]);
+}
+
+// FP64 residual of every not-yet-converged solve: r64 = b64 - D x64.
+template <int N>
+__global__ void __launch_bounds__(128) kb_residual64(BApply b, const double2* coef) {
+  __shared__ double2 ys[4][N];
+  const int warp = threadIdx.x >> 5;
+  const int g = blockIdx.x * 4 + warp;
+  if (g >= b.total) return;
+  const int k = find_solve(b.site_off, b.count, g);
+  const BSolve& s = b.S[b.sidx[k]];
+  if (!bgate(s, b.gate)) return;
+  ApplyArgs a;
+  a.blocks = s.blk64;
+  a.nb = s.nb;
+  a.V = s.V;
+  a.mu = s.mu;
+  a.x = s.x64;
+  a.y = s.r64;
+  a.z = s.b64;
+  a.acc = nullptr;
+  a.coef = coef;
+  a.mode = APPLY_AXPBY;
+  a.adjoint = 0;
+  a.stop = nullptr;
+  a.part = s.part64;
+  a.push = (char*)s.part64 + (size_t)s.N * sizeof(double2);
+  a.cnt = s.cnt;
+  a.err = s.cnt + s.V;
+  apply_site<N, double2, double2, double2>(a, g - b.site_off[k], ys[warp]);
+}
+
 }  // namespace
 
 int launch_apply(int prec, int n, const ApplyArgs& a, cudaStream_t s) {
@@ -589,6 +425,49 @@ int launch_apply(int prec, int n, const ApplyArgs& a, cudaStream_t s) {
   }
   set_error("coarse_apply: unknown precision %d", prec);
   return COARSE_ERR_INVALID_ARG;
+}
+
+}  // namespace coarse
+
+namespace coarse {
+
+int launch_bapply(int prec, int n, const BApply& b, cudaStream_t s) {
+  if (b.total <= 0) return COARSE_OK;
+  const int grid = (b.total + 3) / 4;
+  if (prec == COARSE_PREC_FP32) {
+    switch (n) {
+      case 16: kb_apply<16, float2><<<grid, 128, 0, s>>>(b); break;
+      case 32: kb_apply<32, float2><<<grid, 128, 0, s>>>(b); break;
+      case 48: kb_apply<48, float2><<<grid, 128, 0, s>>>(b); break;
+      default: set_error("batched apply: unsupported n = %d", n); return COARSE_ERR_INVALID_ARG;
+    }
+  } else {
+    switch (n) {
+      case 16: kb_apply<16, cbf16><<<grid, 128, 0, s>>>(b); break;
+      case 32: kb_apply<32, cbf16><<<grid, 128, 0, s>>>(b); break;
+      case 48: kb_apply<48, cbf16><<<grid, 128, 0, s>>>(b); break;
+      default: set_error("batched apply: unsupported n = %d", n); return COARSE_ERR_INVALID_ARG;
+    }
+  }
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
+int launch_bapply64_residual(int n, const BApply& b, cudaStream_t s) {
+  if (b.total <= 0) return COARSE_OK;
+  const int grid = (b.total + 3) / 4;
+  // {-1, +1} for r = -D x + b lives right after the step counter (see the batch layout)
+  const double2* coef = reinterpret_cast<const double2*>(b.step + 4);
+  switch (n) {
+    case 16: kb_residual64<16><<<grid, 128, 0, s>>>(b, coef); break;
+    case 32: kb_residual64<32><<<grid, 128, 0, s>>>(b, coef); break;
+    case 48: kb_residual64<48><<<grid, 128, 0, s>>>(b, coef); break;
+    default: set_error("batched residual: unsupported n = %d", n); return COARSE_ERR_INVALID_ARG;
+  }
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
 }
 
 }  // namespace coarse

@@ -1,0 +1,156 @@
+// Batched lockstep engine: descriptors of the solves that advance together and the
+// launchers of the batched kernels.  One solve = one right-hand-side column of one
+// operator; all solves of a batch run the same phase sequence, each phase is one kernel
+// launch over all solves (work items mapped to solves through prefix sums), and the
+// per-solve stop / active flags on the device skip solves that are finished.
+#pragma once
+
+#include "common.cuh"
+#include "solver_state.cuh"
+
+namespace coarse {
+
+constexpr int kBatchMaxQ = 104;  // dots per reduction (equals the chunked kernels' limit)
+
+struct BSolve {
+  // operator (shared by the solves of one operator)
+  const void* blk;     // inner-precision blocks [V][5][n][n]
+  const void* blk64;   // FP64 blocks
+  const int* nb;       // [V][8]
+  int V, n, N;
+  int kc;              // recycle vectors in use (frozen)
+  double mu;
+  // stencil scratch of this solve (pull partials, pushes, arrival counters + error flag)
+  void* part;
+  void* push;
+  int* cnt;
+  // vectors of the inner precision (complex64)
+  void** vt;           // [m + 1] Krylov basis
+  void** qt;           // [kc + m + 1]: C_k then the basis
+  void** ut;           // [kc + m]: U_k then the basis
+  void* r;
+  void* e;
+  void* t;
+  void* sa;
+  void* sb;
+  void* acc;
+  // FP64 refinement
+  const double2* b64;
+  double2* x64;
+  double2* r64;
+  void* part64;        // FP64 stencil scratch
+  // polynomial chain coefficients (3 per chain step, padded to the batch degree)
+  const double2* polyc;
+  // dense state
+  CycleState* st;
+  Dense dn;
+  double2* h1;
+  double2* h2;
+  double* partial;     // reduction partials of this solve
+  unsigned* counter;   // last-CTA counter of this solve
+  double* norm2;       // [0] ||r||^2 (inner), [1] ||r64||^2, [2] ||b||^2
+  int* flags;          // [0] inner-active this cycle, [1] done (tolerance met)
+  int nch;             // CTAs of this solve in the chunked reductions
+};
+
+// Which vector a batched stencil phase reads / writes.
+enum BSel : int { BS_VJ = 0, BS_VJ1, BS_SA, BS_SB, BS_ACC, BS_T, BS_R };
+
+// Gate of a batched phase: run the solve's part only if ...
+enum BGate : int {
+  BG_STEP = 0,   // ... its Arnoldi cycle is running (st->stop == 0)
+  BG_ACTIVE = 1, // ... it is inner-active this cycle (flags[0])
+  BG_TAIL = 2,   // ... it is inner-active and its cycle made at least one step
+  BG_NOTDONE = 3 // ... it has not met the tolerance (flags[1] == 0)
+};
+
+struct BApply {
+  const BSolve* S;
+  const int* sidx;      // solves of this n-group
+  const int* site_off;  // prefix sums of their site counts (count + 1 entries)
+  int count;
+  int total;            // total sites
+  int mode;             // ApplyMode
+  int xsel, ysel;       // BSel
+  int coef_off;         // offset (in double2) into polyc for POLY modes
+  int gate;             // BGate
+  const int* step;      // device step counter
+};
+
+// work item -> solve, gates and vector selection shared by the batched kernels
+__device__ inline int find_solve(const int* off, int count, int g) {
+  int lo = 0, hi = count;  // off[lo] <= g < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ inline bool bgate(const BSolve& s, int gate) {
+  switch (gate) {
+    case BG_STEP: return s.st->stop == 0;
+    case BG_ACTIVE: return s.flags[0] != 0;
+    case BG_TAIL: return s.flags[0] != 0 && s.st->j > 0;
+    case BG_NOTDONE: return s.flags[1] == 0;
+  }
+  return false;
+}
+
+__device__ inline void* bsel(const BSolve& s, int sel, int step) {
+  switch (sel) {
+    case BS_VJ: return s.vt[step];
+    case BS_VJ1: return s.vt[step + 1];
+    case BS_SA: return s.sa;
+    case BS_SB: return s.sb;
+    case BS_ACC: return s.acc;
+    case BS_T: return s.t;
+    case BS_R: return s.r;
+  }
+  return nullptr;
+}
+
+int launch_bapply(int prec, int n, const BApply& a, cudaStream_t s);
+int launch_bapply64_residual(int n, const BApply& a, cudaStream_t s);
+
+// chunked Gram-Schmidt / vector phases over all solves
+enum BVecOp : int {
+  BV_CGS_DOT = 0,    // h1 = Q^H V[j+1]                    (gate step)
+  BV_CGS_UPDDOT,     // V[j+1] -= Q h1 ; h2 = Q^H V[j+1]      (gate step)
+  BV_CGS_UPDNORM,    // V[j+1] -= Q h2 ; st->wnorm2           (gate step)
+  BV_PROJ_DOT,       // ycoef = C^H r                         (gate active, kc > 0)
+  BV_PROJ_UPD,       // r -= C ycoef ; norm2[0]               (gate active)
+  BV_RES_UPD,        // r -= V[0..j] z ; norm2[0]             (gate tail)
+  BV_NORM_R,         // norm2[0] = ||r||^2                     (gate active)
+};
+int launch_bvec(int op, const BSolve* S, int nsolves, const int* chunk_off, int total_chunks, int E,
+                const int* step, cudaStream_t s);
+
+// per-solve elementwise phases
+enum BElem : int {
+  BE_NORMALIZE = 0,  // V[j+1] *= inv_h if the finalize of step j ran
+  BE_START,          // V[0] = r * inv_h                       (gate step)
+  BE_COMBINE_T,      // t = ut[0..kc+j) . ycoef                (gate tail)
+  BE_COMBINE_U,      // t = U_k . ycoef[0..kc)                 (gate active, kc > 0)
+  BE_AXPY_E,         // e += acc                                (gate tail / active)
+  BE_AXPY_E_PROJ,    // e += acc after the projection          (gate active, kc > 0)
+  BE_TO_LOW,         // r = r64 / ||r64||, e = 0                (gate not done)
+  BE_ADD_LOW,        // x64 += ||r64|| e                        (gate not done)
+  BE_ZERO_X,         // x64 = 0                                 (all)
+};
+// aux: source of BE_AXPY_E (BS_ACC or BS_T); gate: BGate of BE_AXPY_E
+int launch_belem(int op, const BSolve* S, int nsolves, const int* chunk_off, int total_chunks, int E,
+                 const int* step, int aux, int gate, cudaStream_t s);
+
+// per-solve dense kernels (one CTA per solve)
+int launch_bcycle_init(const BSolve* S, int nsolves, int m, double target, cudaStream_t s);
+int launch_bfinalize(const BSolve* S, int nsolves, cudaStream_t s);
+int launch_bcycle_solve(const BSolve* S, int nsolves, cudaStream_t s);
+// which = 1: norm2[1] = ||r64||^2, which = 2: norm2[2] = ||b64||^2
+int launch_bnorms64(const BSolve* S, int nsolves, const int* chunk_off, int total_chunks, int E, int which,
+                    cudaStream_t s);
+int batch_chunk_elems(int maxN);     // elements per lane of the chunked kernels for the largest solve
+int batch_chunks(int N, int E);      // CTAs of one solve
+int launch_step_inc(int* step, cudaStream_t s);
+
+}  // namespace coarse

@@ -9,6 +9,7 @@
 // deterministic and no second launch is needed.
 #include "common.cuh"
 #include "solver_state.cuh"
+#include "batch.cuh"
 
 namespace coarse {
 namespace {
@@ -89,6 +90,7 @@ __device__ bool last_block(unsigned* counter, unsigned total) {
 // stays in registers while the kernel sweeps all basis vectors.
 constexpr int kW = 8;
 constexpr int kMaxQ = 104;  // largest nq + 1 handled in one launch
+static_assert(kMaxQ == kBatchMaxQ, "batched reductions size their partials with kBatchMaxQ");
 
 template <class C> __device__ __forceinline__ float2 to_f2(C v) { return make_float2(float(v.x), float(v.y)); }
 
@@ -170,17 +172,17 @@ __device__ __forceinline__ void chunk_dots(const double2* const* q, int nq, cons
 
 // CTA partials (sum over warps in FP64) to the global partial array, then the last CTA reduces.
 __device__ void cta_finish(const double2* wp /*[kW][kMaxQ]*/, int nout, double* partial, unsigned* counter,
-                           double2* out, double* wnorm2, int norm_slot) {
+                           double2* out, double* wnorm2, int norm_slot, int cta = -1, int nch = -1) {
   __syncthreads();
-  const int nch = gridDim.x;
+  if (cta < 0) { cta = blockIdx.x; nch = gridDim.x; }
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
     double re = 0.0, im = 0.0;
 #pragma unroll
     for (int w = 0; w < kW; ++w) { re += wp[w * kMaxQ + o].x; im += wp[w * kMaxQ + o].y; }
-    partial[(size_t)(2 * o) * nch + blockIdx.x] = re;
-    partial[(size_t)(2 * o + 1) * nch + blockIdx.x] = im;
+    partial[(size_t)(2 * o) * nch + cta] = re;
+    partial[(size_t)(2 * o + 1) * nch + cta] = im;
   }
-  if (last_block(counter, gridDim.x)) {
+  if (last_block(counter, nch)) {
     finish(partial, nout, nch, out, wnorm2, norm_slot);
     if (threadIdx.x == 0) *counter = 0;
   }
@@ -424,6 +426,182 @@ int elem_grid(int N) {
   return g > 152 * 8 ? 152 * 8 : (g < 1 ? 1 : g);
 }
 
+// ------------------------------------------------------------------------------------------
+// Batched chunked vector phases: CTA c of the flat grid belongs to the solve found through
+// the chunk prefix sums and works on its chunk (c - chunk_off[solve]) of that solve's
+// vectors; reductions finish per solve (the solve's own counter and partials).
+template <int E>
+__global__ void __launch_bounds__(32 * kW) kb_vec(int op, const BSolve* S, int nsolves, const int* chunk_off,
+                                                 const int* step_ptr) {
+  __shared__ double2 wp[kW * kMaxQ];
+  __shared__ float2 hc[kMaxQ];
+  const int k = find_solve(chunk_off, nsolves, blockIdx.x);
+  const BSolve& s = S[k];
+  const int cta = blockIdx.x - chunk_off[k];
+  const int step = *step_ptr;
+  bool run;
+  switch (op) {
+    case BV_CGS_DOT: case BV_CGS_UPDDOT: case BV_CGS_UPDNORM: run = bgate(s, BG_STEP); break;
+    case BV_PROJ_DOT: case BV_PROJ_UPD: run = bgate(s, BG_ACTIVE) && s.kc > 0; break;
+    case BV_RES_UPD: run = bgate(s, BG_TAIL); break;
+    default: run = bgate(s, BG_ACTIVE); break;
+  }
+  if (!run) return;  // uniform over the solve's CTAs
+  const float2* const* q = (const float2* const*)(s.kc > 0 ? s.qt : s.vt);
+  float2* w = nullptr;
+  int nq = 0, upd = 0, dots = 0, norm = 0;
+  const double2* h = nullptr;
+  double2* out = nullptr;
+  double* nout = nullptr;
+  switch (op) {
+    case BV_CGS_DOT: w = (float2*)s.vt[step + 1]; nq = s.kc + step + 1; dots = 1; out = s.h1; break;
+    case BV_CGS_UPDDOT: w = (float2*)s.vt[step + 1]; nq = s.kc + step + 1; upd = 1; h = s.h1; dots = 1; out = s.h2; break;
+    case BV_CGS_UPDNORM: w = (float2*)s.vt[step + 1]; nq = s.kc + step + 1; upd = 1; h = s.h2; norm = 1;
+      nout = &s.st->wnorm2; break;
+    case BV_PROJ_DOT: q = (const float2* const*)s.qt; w = (float2*)s.r; nq = s.kc; dots = 1; out = s.dn.ycoef; break;
+    case BV_PROJ_UPD: q = (const float2* const*)s.qt; w = (float2*)s.r; nq = s.kc; upd = 1; h = s.dn.ycoef; norm = 1;
+      nout = s.norm2; break;
+    case BV_RES_UPD: q = (const float2* const*)s.vt; w = (float2*)s.r; nq = s.st->j + 1; upd = 1; h = s.dn.z; norm = 1;
+      nout = s.norm2; break;
+    default: w = (float2*)s.r; nq = 0; norm = 1; nout = s.norm2; break;
+  }
+  const int N = s.N;
+  if (upd) {
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) hc[i] = make_float2(float(-h[i].x), float(-h[i].y));
+    __syncthreads();
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long base = ((long long)cta * kW + warp) * 32 * E;
+  float2 wv[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const long long idx = base + lane + 32 * e;
+    wv[e] = idx < N ? w[idx] : make_float2(0.f, 0.f);
+  }
+  if (upd) {
+    for (int i = 0; i < nq; ++i) {
+      const float2* qi = q[i];
+      const float2 hi = hc[i];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const long long idx = base + lane + 32 * e;
+        if (idx < N) cfma(wv[e], qi[idx], hi);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long idx = base + lane + 32 * e;
+      if (idx < N) w[idx] = wv[e];
+    }
+  }
+  if (dots) {
+    chunk_dots(q, nq, wv, base, N, lane, wp + warp * kMaxQ);
+    cta_finish(wp, nq + 1, s.partial, s.counter, out, nullptr, nq, cta, s.nch);
+  } else if (norm) {
+    chunk_dots(q, 0, wv, base, N, lane, wp + warp * kMaxQ);
+    cta_finish(wp, 1, s.partial, s.counter, nullptr, nout, 0, cta, s.nch);
+  }
+}
+
+// Batched elementwise phases (same chunk mapping).
+template <int E>
+__global__ void __launch_bounds__(32 * kW) kb_elem(int op, const BSolve* S, int nsolves, const int* chunk_off,
+                                                  const int* step_ptr, int aux, int gate) {
+  __shared__ float2 cf[kMaxQ];
+  const int k = find_solve(chunk_off, nsolves, blockIdx.x);
+  const BSolve& s = S[k];
+  const int cta = blockIdx.x - chunk_off[k];
+  const int step = *step_ptr;
+  bool run = true;
+  switch (op) {
+    case BE_NORMALIZE: run = s.st->j == step + 1; break;
+    case BE_START: run = bgate(s, BG_STEP); break;
+    case BE_COMBINE_T: run = bgate(s, BG_TAIL); break;
+    case BE_COMBINE_U: run = bgate(s, BG_ACTIVE) && s.kc > 0; break;
+    case BE_AXPY_E: run = bgate(s, gate); break;
+    case BE_AXPY_E_PROJ: run = bgate(s, BG_ACTIVE) && s.kc > 0; break;
+    case BE_TO_LOW: case BE_ADD_LOW: run = bgate(s, BG_NOTDONE); break;
+    default: run = true; break;
+  }
+  if (!run) return;
+  const int N = s.N;
+  int nin = 0;
+  const float2* const* in = nullptr;
+  if (op == BE_COMBINE_T || op == BE_COMBINE_U) {
+    nin = op == BE_COMBINE_T ? s.kc + s.st->j : s.kc;
+    in = (const float2* const*)(s.kc > 0 ? s.ut : s.vt);
+    for (int i = threadIdx.x; i < nin; i += blockDim.x)
+      cf[i] = make_float2(float(s.dn.ycoef[i].x), float(s.dn.ycoef[i].y));
+    __syncthreads();
+  }
+  const double inv_h = s.st->inv_h;
+  const double rn = sqrt(fmax(s.norm2[1], 0.0));
+  const long long cbase = (long long)cta * kW * 32 * E;
+  for (long long idx = cbase + threadIdx.x; idx < cbase + (long long)kW * 32 * E && idx < N; idx += blockDim.x) {
+    switch (op) {
+      case BE_NORMALIZE: {
+        float2* v = (float2*)s.vt[step + 1];
+        const float2 a = v[idx];
+        v[idx] = make_float2(float(a.x * inv_h), float(a.y * inv_h));
+      } break;
+      case BE_START: {
+        const float2 a = ((const float2*)s.r)[idx];
+        ((float2*)s.vt[0])[idx] = make_float2(float(a.x * inv_h), float(a.y * inv_h));
+      } break;
+      case BE_COMBINE_T:
+      case BE_COMBINE_U: {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i = 0; i < nin; ++i) cfma(acc, in[i][idx], cf[i]);
+        ((float2*)s.t)[idx] = acc;
+      } break;
+      case BE_AXPY_E:
+      case BE_AXPY_E_PROJ: {
+        const float2 a = ((const float2*)(aux == BS_T ? s.t : s.acc))[idx];
+        float2* ev = (float2*)s.e;
+        const float2 b = ev[idx];
+        ev[idx] = make_float2(b.x + a.x, b.y + a.y);
+      } break;
+      case BE_TO_LOW: {
+        const double2 a = s.r64[idx];
+        const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+        ((float2*)s.r)[idx] = make_float2(float(a.x * inv), float(a.y * inv));
+        ((float2*)s.e)[idx] = make_float2(0.f, 0.f);
+      } break;
+      case BE_ADD_LOW: {
+        const float2 d = ((const float2*)s.e)[idx];
+        double2 x = s.x64[idx];
+        x.x = fma(rn, double(d.x), x.x);
+        x.y = fma(rn, double(d.y), x.y);
+        s.x64[idx] = x;
+      } break;
+      default: s.x64[idx] = make_double2(0.0, 0.0); break;
+    }
+  }
+}
+
+// ||r64||^2 (and ||b64||^2) of every not-yet-converged solve.
+template <int E>
+__global__ void __launch_bounds__(32 * kW) kb_norm64(const BSolve* S, int nsolves, const int* chunk_off, int which) {
+  __shared__ double2 wp[kW * kMaxQ];
+  const int k = find_solve(chunk_off, nsolves, blockIdx.x);
+  const BSolve& s = S[k];
+  if (!bgate(s, BG_NOTDONE)) return;
+  const int cta = blockIdx.x - chunk_off[k];
+  const double2* v = which == 1 ? s.r64 : s.b64;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long base = ((long long)cta * kW + warp) * 32 * E;
+  double nn = 0.0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const long long idx = base + lane + 32 * e;
+    if (idx < s.N) { const double2 a = v[idx]; nn += a.x * a.x + a.y * a.y; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
+  if (lane == 0) wp[warp * kMaxQ] = make_double2(nn, 0.0);
+  cta_finish(wp, 1, s.partial, s.counter, nullptr, s.norm2 + which, 0, cta, s.nch);
+}
+
 }  // namespace
 
 namespace {
@@ -581,5 +759,45 @@ int launch_check_finite(int prec64, const void* x, int N, int* flag, cudaStream_
   COARSE_CUDA(cudaGetLastError());
   return COARSE_OK;
 }
+
+}  // namespace coarse
+
+namespace coarse {
+
+int launch_bvec(int op, const BSolve* S, int nsolves, const int* chunk_off, int total_chunks, int E, const int* step,
+                cudaStream_t s) {
+  if (total_chunks <= 0) return COARSE_OK;
+  if (E == 4) kb_vec<4><<<total_chunks, 32 * kW, 0, s>>>(op, S, nsolves, chunk_off, step);
+  else if (E == 8) kb_vec<8><<<total_chunks, 32 * kW, 0, s>>>(op, S, nsolves, chunk_off, step);
+  else kb_vec<16><<<total_chunks, 32 * kW, 0, s>>>(op, S, nsolves, chunk_off, step);
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
+int launch_belem(int op, const BSolve* S, int nsolves, const int* chunk_off, int total_chunks, int E, const int* step,
+                 int aux, int gate, cudaStream_t s) {
+  if (total_chunks <= 0) return COARSE_OK;
+  if (E == 4) kb_elem<4><<<total_chunks, 32 * kW, 0, s>>>(op, S, nsolves, chunk_off, step, aux, gate);
+  else if (E == 8) kb_elem<8><<<total_chunks, 32 * kW, 0, s>>>(op, S, nsolves, chunk_off, step, aux, gate);
+  else kb_elem<16><<<total_chunks, 32 * kW, 0, s>>>(op, S, nsolves, chunk_off, step, aux, gate);
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
+int launch_bnorms64(const BSolve* S, int nsolves, const int* chunk_off, int total_chunks, int E, int which,
+                    cudaStream_t s) {
+  if (total_chunks <= 0) return COARSE_OK;
+  if (E == 4) kb_norm64<4><<<total_chunks, 32 * kW, 0, s>>>(S, nsolves, chunk_off, which);
+  else if (E == 8) kb_norm64<8><<<total_chunks, 32 * kW, 0, s>>>(S, nsolves, chunk_off, which);
+  else kb_norm64<16><<<total_chunks, 32 * kW, 0, s>>>(S, nsolves, chunk_off, which);
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
+int batch_chunk_elems(int maxN) { return chunk_elems(maxN); }
+int batch_chunks(int N, int E) { return chunk_grid(N, E); }
 
 }  // namespace coarse

@@ -13,6 +13,7 @@
 #include "common.cuh"
 #include "dense.cuh"
 #include "solver_state.cuh"
+#include "batch.cuh"
 
 namespace coarse {
 namespace {
@@ -40,12 +41,12 @@ __global__ void k_cycle_init(CycleState* st, int k, int steps, const double* rno
 
 // One warp.  Loads and stores are lane-parallel; only the j rotations of the new
 // column (inherently sequential) and the new rotation run on lane 0.
-__global__ void __launch_bounds__(32) k_step_finalize(CycleState* st, const double2* h1, const double2* h2, Dense d) {
+__device__ void finalize_warp(CycleState* st, const double2* h1, const double2* h2, const Dense& d) {
   __shared__ double2 col[kMaxDense + 2];
   __shared__ double csh[kMaxDense];
   __shared__ double2 snh[kMaxDense];
   __shared__ double hn2s;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31;
   if (st->stop) return;  // every lane reads the same flag
   const int j = st->j, k = st->k, ldh = d.ldh;
   double hn2 = 0.0;
@@ -112,12 +113,21 @@ __global__ void __launch_bounds__(32) k_step_finalize(CycleState* st, const doub
   if (lane == 0) st->j = j + 1;  // last: the normalisation kernel of this step keys on st->j == j + 1
 }
 
+__global__ void __launch_bounds__(32) k_step_finalize(CycleState* st, const double2* h1, const double2* h2, Dense d) {
+  finalize_warp(st, h1, h2, d);
+}
+
+__global__ void __launch_bounds__(32) kb_finalize(const BSolve* S) {
+  const BSolve& s = S[blockIdx.x];
+  finalize_warp(s.st, s.h1, s.h2, s.dn);
+}
+
 // One warp: y = R^{-1} g by column-oriented back substitution (R staged in shared memory,
 // lane r owns right-hand-side rows r and r + 32), then y_U = -B y_V and z = Hbar y_V.
-__global__ void __launch_bounds__(32) k_cycle_solve(const CycleState* st, Dense d) {
+__device__ void cycle_solve_warp(const CycleState* st, const Dense& d) {
   extern __shared__ double2 Rs[];  // kMaxDense columns of d.ldh entries
   __shared__ double2 ys[kMaxDense];
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const int j = st->j, k = st->k, ldh = d.ldh;
   for (int e = lane; e < j * ldh; e += 32) Rs[e] = d.R[e];
   double2 x0 = lane < j ? d.g[lane] : make_double2(0.0, 0.0);
@@ -146,6 +156,48 @@ __global__ void __launch_bounds__(32) k_cycle_solve(const CycleState* st, Dense 
     for (int l = (i > 0 ? i - 1 : 0); l < j; ++l) s = add(s, mul(d.H[l * ldh + i], ys[l]));
     d.z[i] = s;
   }
+}
+
+__global__ void __launch_bounds__(32) k_cycle_solve(const CycleState* st, Dense d) { cycle_solve_warp(st, d); }
+
+__global__ void __launch_bounds__(32) kb_cycle_solve(const BSolve* S) {
+  const BSolve& s = S[blockIdx.x];
+  if (!bgate(s, BG_TAIL)) return;
+  cycle_solve_warp(s.st, s.dn);
+}
+
+// start of a cycle for every inner-active solve; inactive solves are stopped.
+// target: relative to the inner right-hand side, whose norm is 1 at the start of a refinement
+// step (per-solve target in norm2[3]).
+__global__ void kb_cycle_init(const BSolve* S, int m) {
+  const BSolve& s = S[blockIdx.x];
+  if (threadIdx.x != 0) return;
+  CycleState* st = s.st;
+  st->j = 0;
+  st->rstatus = 0;
+  if (!s.flags[0]) {
+    st->stop = 1;
+    st->status = 0;
+    return;
+  }
+  const double beta = sqrt(fmax(s.norm2[0], 0.0));
+  st->k = s.kc;
+  st->steps = s.kc > 0 ? m - s.kc : m;
+  st->stop = 0;
+  st->status = 0;
+  st->beta = beta;
+  st->target = s.norm2[3];
+  st->resid = beta;
+  st->inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
+  s.dn.g[0] = make_double2(beta, 0.0);
+  if (!(beta > 0.0) || !isfinite(beta)) {
+    st->stop = 1;
+    st->status = isfinite(beta) ? ST_ZERO : ST_NONFINITE;
+  }
+}
+
+__global__ void kb_step_inc(int* step) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
 }
 
 // Harmonic Ritz vectors of the cycle just finished and the coefficients of
@@ -390,6 +442,47 @@ int launch_poly_roots(CycleState* st, const Dense& d, int dmax, cudaStream_t s) 
     attr = true;
   }
   k_poly_roots<<<1, 32, smem, s>>>(st, d, dmax);
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
+}  // namespace coarse
+
+namespace coarse {
+
+int launch_bcycle_init(const BSolve* S, int nsolves, int m, double /*target*/, cudaStream_t s) {
+  if (nsolves <= 0) return COARSE_OK;
+  kb_cycle_init<<<nsolves, 32, 0, s>>>(S, m);
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
+int launch_bfinalize(const BSolve* S, int nsolves, cudaStream_t s) {
+  if (nsolves <= 0) return COARSE_OK;
+  kb_finalize<<<nsolves, 32, 0, s>>>(S);
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
+int launch_bcycle_solve(const BSolve* S, int nsolves, cudaStream_t s) {
+  if (nsolves <= 0) return COARSE_OK;
+  static bool attr = false;
+  const size_t smem = sizeof(double2) * (size_t)kMaxDense * (kMaxDense + 1);
+  if (!attr) {
+    COARSE_CUDA(cudaFuncSetAttribute(kb_cycle_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  kb_cycle_solve<<<nsolves, 32, smem, s>>>(S);
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
+int launch_step_inc(int* step, cudaStream_t s) {
+  kb_step_inc<<<1, 32, 0, s>>>(step);
   note_launch();
   COARSE_CUDA(cudaGetLastError());
   return COARSE_OK;
