@@ -397,6 +397,65 @@ def run_apply_only(args):
     cop.close()
 
 
+def run_batched(args):
+    """Uneven batch of coarse solves (coarse 4^4 / 6^4 / 8^4, nv 8 / 16 / 24, 1-12 right-hand sides
+    each, m0 in [-0.44, -0.38]): the lockstep engine vs the single-operator path on the same inputs."""
+    import torch
+
+    import paper_2205_09104_gb300 as cg
+    from synthetic import draws
+    from synthetic.coarse_op import build_coarse_operator
+    dev = torch.device("cuda", 0)
+    prec = cg.PREC_BF16 if args.prec == "bf16" else cg.PREC_FP32
+    recipe = draws.batch_recipe((4, 0), args.batched)
+    t = time.perf_counter()
+    ops, bs, xs = [], [], []
+    for i, (L, nv, m0, nr) in enumerate(recipe):
+        op = build_coarse_operator((4, 1 + i), (2 * L,) * 4, nv, m0, CSW, device=dev)
+        ops.append(cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(prec,), max_nrhs=12))
+        N = op.volume * op.n
+        bs.append(torch.from_numpy(draws.rhs((4, 1 + i, 7), nr, N)).to(dev))
+        xs.append(torch.zeros_like(bs[-1]))
+        del op
+    t_gen = time.perf_counter() - t
+    inner_tol = 1e-5 if prec == cg.PREC_FP32 else 1e-2
+    p = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS, **PARAMS)
+    t = time.perf_counter()
+    cg.solve_batched(ops, bs, xs, p)          # setup (polynomials, recycle spaces) + first batch
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t
+    for _ in range(args.warmup):
+        cg.solve_batched(ops, bs, xs, p)
+    torch.cuda.synchronize()
+    nrhs = sum(b.shape[0] for b in bs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        infos = []
+        for _ in range(args.steps):
+            infos = cg.solve_batched(ops, bs, xs, p)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    worst = max(i["rel_residual"] for i in infos)
+    # the same columns through the single-operator path, one operator after another
+    e0.record()
+    for o, b, x in zip(ops, bs, xs):
+        o.solve(b, x, params=p)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    print(json.dumps({"mode": "batched", "operators": len(ops), "right_hand_sides": nrhs,
+                      "precision": args.prec, "ms_per_batch": round(ms, 2),
+                      "rhs_solves_per_s": round(nrhs / (ms / 1e3), 1), "operator_batches_per_s": round(1e3 / ms, 3),
+                      "sequential_ms": round(ms_seq, 2), "speedup_vs_sequential": round(ms_seq / ms, 2),
+                      "worst_rel_residual": worst, "kernel_launches_per_batch": infos[0]["kernel_launches"],
+                      "generate_s": round(t_gen, 1), "setup_s": round(t_setup, 2), "clocks": clk.summary()}),
+          flush=True)
+    for o in ops:
+        o.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,7 +470,12 @@ def main():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--fp64-baseline-steps", type=int, default=2,
                     help="plain FP64 GMRES(50) solves timed for the speedup (0 = skip)")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="time the lockstep batched engine on this many uneven operators")
     args = ap.parse_args()
+    if args.batched:
+        run_batched(args)
+        return
     if args.apply_only:
         run_apply_only(args)
         return

@@ -69,23 +69,27 @@ class FineOperator:
     gamma: torch.Tensor    # (4, 4, 4)
 
     def hop(self, d: int, psi: torch.Tensor) -> torch.Tensor:
-        """Term of D for hop direction d applied to psi (V, 4, 3)."""
+        """Term of D for hop direction d applied to psi (..., V, 4, 3)."""
         mu = d % 4
+        V = psi.shape[-3]
+        lead = psi.shape[:-3]
         eye = torch.eye(4, dtype=psi.dtype, device=psi.device)
         if d < 4:
             proj = -0.5 * (eye - self.gamma[mu])
             link = self.U[mu]
-            src = psi[self.nb[:, d]]
         else:
             proj = -0.5 * (eye + self.gamma[mu])
             link = self.U[mu][self.nb[:, d]].conj().transpose(-1, -2)
-            src = psi[self.nb[:, d]]
-        t = torch.einsum("vab,vsb->vsa", link, src)
-        return torch.einsum("st,vta->vsa", proj, t)
+        src = psi.index_select(-3, self.nb[:, d]).reshape(-1, V, 4, 3)   # (C, V, 4, 3)
+        C = src.shape[0]
+        x = src.permute(1, 3, 0, 2).reshape(V, 3, C * 4)                # colour-major per site
+        t = torch.bmm(link, x).reshape(V, 3, C, 4).permute(2, 0, 3, 1)   # (C, V, 4, 3)
+        return torch.matmul(proj, t).reshape(*lead, V, 4, 3)
 
     def diag(self, psi: torch.Tensor) -> torch.Tensor:
-        V = psi.shape[0]
-        return torch.einsum("vij,vj->vi", self.clover, psi.reshape(V, 12)).reshape(V, 4, 3)
+        shp = psi.shape
+        out = torch.matmul(self.clover, psi.reshape(-1, shp[-3], 12, 1))
+        return out.reshape(shp)
 
     def apply(self, psi: torch.Tensor) -> torch.Tensor:
         out = self.diag(psi)
@@ -146,34 +150,51 @@ def fine_operator(key, dims, m0: float, csw: float, eps: float = 0.3, device="cp
     return FineOperator(tuple(dims), U, cl, nb, coords, g)
 
 
+def _chunk(count: int, per_item_bytes: int, device) -> int:
+    """Items processed together: batched on a GPU (within a memory budget), one at a time on the host."""
+    if not str(device).startswith("cuda"):
+        return 1
+    return max(1, min(count, (24 << 30) // max(per_item_bytes, 1)))
+
+
 def refine_test_vectors(D: FineOperator, starts: torch.Tensor, iters: int) -> torch.Tensor:
-    """Each start x0 -> argmin ||D x|| over x0 + K_iters(D, D x0) (one unrestarted GMRES cycle on D x = 0)."""
+    """Each start x0 -> argmin ||D x|| over x0 + K_iters(D, D x0) (one unrestarted GMRES cycle on D x = 0).
+
+    The starts are processed together in chunks (modified Gram-Schmidt per vector, batched)."""
+    nv = starts.shape[0]
+    V = starts.shape[1]
+    dev = starts.device
+    per = (iters + 4) * V * 12 * 16
+    ch = _chunk(nv, per, dev)
     out = []
-    for x0 in starts:
-        r0 = -D.apply(x0)
-        beta = torch.linalg.vector_norm(r0)
-        basis = [r0 / beta]
-        H = torch.zeros((iters + 1, iters), dtype=torch.complex128, device=x0.device)
-        m = iters
+    red = tuple(range(1, starts.dim()))
+    for c0 in range(0, nv, ch):
+        X0 = starts[c0:c0 + ch]
+        nb_ = X0.shape[0]
+        r0 = -D.apply(X0)
+        beta = torch.linalg.vector_norm(r0, dim=red)
+        shape1 = (nb_,) + (1,) * (X0.dim() - 1)
+        basis = [r0 / beta.reshape(shape1)]
+        H = torch.zeros((nb_, iters + 1, iters), dtype=torch.complex128, device=dev)
         for j in range(iters):
             w = D.apply(basis[j])
             for i in range(j + 1):
-                H[i, j] = torch.vdot(basis[i].reshape(-1), w.reshape(-1))
-                w = w - H[i, j] * basis[i]
-            H[j + 1, j] = torch.linalg.vector_norm(w)
-            if H[j + 1, j].abs() == 0:
-                m = j + 1
-                break
-            basis.append(w / H[j + 1, j])
-        rhs = torch.zeros(m + 1, dtype=torch.complex128, device=x0.device)
-        rhs[0] = beta
-        # small least-squares problem on the host (any device gives the same arithmetic)
-        z = torch.linalg.lstsq(H[: m + 1, :m].cpu(), rhs[:, None].cpu()).solution[:, 0].to(x0.device)
-        x = x0.clone()
-        for i in range(m):
-            x = x + z[i] * basis[i]
+                h = (basis[i].conj() * w).sum(dim=red)
+                H[:, i, j] = h
+                w = w - h.reshape(shape1) * basis[i]
+            hn = torch.linalg.vector_norm(w, dim=red)
+            H[:, j + 1, j] = hn
+            basis.append(w / hn.reshape(shape1))
+        rhs = torch.zeros((nb_, iters + 1, 1), dtype=torch.complex128)
+        rhs[:, 0, 0] = beta.cpu()
+        # small least-squares problems on the host (any device gives the same arithmetic)
+        z = torch.linalg.lstsq(H.cpu(), rhs).solution[:, :, 0].to(dev)
+        x = X0.clone()
+        for i in range(iters):
+            x = x + z[:, i].reshape(shape1) * basis[i]
         out.append(x)
-    return torch.stack(out)
+        del basis
+    return torch.cat(out)
 
 
 def prolongator(tv: torch.Tensor, dims) -> torch.Tensor:
@@ -212,30 +233,50 @@ def _restrict(Pf: torch.Tensor, w: torch.Tensor, dims) -> torch.Tensor:
 
 
 def galerkin(D: FineOperator, Pf: torch.Tensor):
-    """Blocks of D_c = P^H D P, separated into the self block and the 8 hop directions."""
+    """Blocks of D_c = P^H D P, separated into the self block and the 8 hop directions.
+
+    The columns (h, k) of P are pushed through the operator together in chunks."""
     dims = D.dims
     nv = Pf.shape[-1]
     n = 2 * nv
-    Vc = lattice_volume(dims) // 16
+    V = lattice_volume(dims)
+    Vc = V // 16
     dev = Pf.device
     self_b = torch.zeros((Vc, n, n), dtype=torch.complex128, device=dev)
     hop_b = torch.zeros((Vc, 8, n, n), dtype=torch.complex128, device=dev)
     chir_of_spin = torch.tensor([0, 0, 1, 1], device=dev)
+    ch = _chunk(nv, 8 * V * 12 * 16, dev)
+    inside = []
+    for d in range(8):
+        par = D.coords[d % 4] % 2
+        m = (par == 0) if d < 4 else (par == 1)     # x +- mu stays in the aggregate
+        inside.append(m.to(torch.complex128)[:, None, None])
     for h in range(2):
-        smask = (chir_of_spin == h).to(torch.complex128)[None, :, None]
-        for k in range(nv):
-            col = h * nv + k
-            phi = Pf[..., k] * smask                            # column (h, k) on every aggregate
-            self_b[:, :, col] += _restrict(Pf, D.diag(phi), dims)
+        smask = (chir_of_spin == h).to(torch.complex128)[None, None, :, None]
+        for k0 in range(0, nv, ch):
+            ks = slice(k0, min(nv, k0 + ch))
+            phi = Pf[..., ks].permute(3, 0, 1, 2) * smask       # columns (h, k) on every aggregate
+            cols = slice(h * nv + k0, h * nv + ks.stop)
+            self_b[:, :, cols] += _restrict_many(Pf, D.diag(phi), dims)
             for d in range(8):
-                mu = d % 4
-                par = D.coords[mu] % 2
-                inside = (par == 0) if d < 4 else (par == 1)    # x +- mu stays in the aggregate
                 hp = D.hop(d, phi)
-                m_in = inside.to(torch.complex128)[:, None, None]
-                self_b[:, :, col] += _restrict(Pf, hp * m_in, dims)
-                hop_b[:, d, :, col] += _restrict(Pf, hp * (1 - m_in), dims)
+                self_b[:, :, cols] += _restrict_many(Pf, hp * inside[d], dims)
+                hop_b[:, d, :, cols] += _restrict_many(Pf, hp * (1 - inside[d]), dims)
     return self_b, hop_b
+
+
+def _restrict_many(Pf: torch.Tensor, w: torch.Tensor, dims) -> torch.Tensor:
+    """(P^H w_c) for a stack of fine vectors w (C, V, 4, 3); returns (Vc, n, C)."""
+    nv = Pf.shape[-1]
+    C = w.shape[0]
+    L0, L1, L2, L3 = dims
+    # (V, 4, 3*nv)^H-contraction per site, batched over the C vectors
+    t = torch.bmm(w.reshape(C, -1, 4, 3).permute(1, 2, 0, 3).reshape(-1, C, 3),
+                  Pf.conj().reshape(-1, 3, nv))                    # (V*4, C, nv)
+    t = t.reshape(-1, 2, 2, C, nv).sum(2)                          # (V, chir, C, nv)
+    t = t.permute(2, 0, 1, 3).reshape(C, L3 // 2, 2, L2 // 2, 2, L1 // 2, 2, L0 // 2, 2, 2 * nv)
+    t = t.sum((2, 4, 6, 8)).reshape(C, -1, 2 * nv)                 # (C, Vc, n)
+    return t.permute(1, 2, 0)
 
 
 @dataclass

@@ -11,6 +11,7 @@ Streams:
     2  right-hand sides
     3  polynomial start vector
     4  loss vector ``c`` and finite-difference entry picks
+    5  recipe of a batch of uneven operators
 """
 from __future__ import annotations
 
@@ -21,6 +22,7 @@ STREAM_TESTVEC = 1
 STREAM_RHS = 2
 STREAM_POLY = 3
 STREAM_GRAD = 4
+STREAM_BATCH = 5
 
 
 def rng(key, stream: int) -> np.random.Generator:
@@ -75,3 +77,13 @@ def grad_draws(key, n_unknowns: int, volume: int, n: int, picks: int):
     ent = np.stack([gen.integers(0, volume, picks), gen.integers(0, 9, picks),
                     gen.integers(0, n, picks), gen.integers(0, n, picks)], axis=1)
     return c, b, ent
+
+
+def batch_recipe(key, count: int, extents=(4, 6, 8), nvs=(8, 16, 24), m0_range=(-0.44, -0.38), max_rhs=12):
+    """Uneven batch: per operator (coarse extent L, nv, m0, number of right-hand sides)."""
+    gen = rng(key, STREAM_BATCH)
+    L = gen.choice(extents, size=count)
+    nv = gen.choice(nvs, size=count)
+    m0 = gen.uniform(m0_range[0], m0_range[1], size=count)
+    nr = gen.integers(1, max_rhs + 1, size=count)
+    return [(int(L[i]), int(nv[i]), float(m0[i]), int(nr[i])) for i in range(count)]
