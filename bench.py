@@ -397,6 +397,57 @@ def run_apply_only(args):
     cop.close()
 
 
+def run_mrhs(args):
+    """Multi-right-hand-side BF16 apply on tensor cores vs one single-column BF16 apply per column:
+    coarse 4^4 / 6^4 / 8^4 (V = 256, 1296, 4096), n = 16 / 32 / 48, 1-12 columns; L2 flushed
+    (256 MB write) before every timed launch."""
+    import torch
+
+    import paper_2205_09104_gb300 as cg
+    from synthetic.coarse_op import build_coarse_operator
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak, src = peaks()
+    g = torch.Generator(device="cpu").manual_seed(6)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for L in (4, 6, 8):
+        for nv in (8, 16, 24):
+            op = build_coarse_operator((6, L, nv), (2 * L,) * 4, nv, -0.42, CSW, device=dev)
+            cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(cg.PREC_BF16,),
+                              max_nrhs=12)
+            del op
+            n, V = 2 * nv, cop.V
+            N = n * V
+            for nrhs in (1, 2, 4, 8, 12):
+                X = torch.randn(nrhs, N, dtype=torch.complex64, generator=g).to(dev)
+                Y = torch.empty_like(X)
+                t_m = timed(lambda: cop.apply(X, precision=cg.PREC_BF16, out=Y))
+                t_c = timed(lambda: [cop.apply(X[c], precision=cg.PREC_BF16, out=Y[c]) for c in range(nrhs)])
+                nbytes = 5 * n * n * 4 * V + 2 * nrhs * N * 8
+                flops = 9 * n * n * 8 * V * nrhs
+                print(json.dumps({"mode": "mrhs", "coarse": f"{L}^4", "V": V, "n": n, "nrhs": nrhs,
+                                  "us_mrhs": round(t_m * 1e3, 2), "us_per_column_path": round(t_c * 1e3, 2),
+                                  "speedup": round(t_c / t_m, 2),
+                                  "achieved_gbs": round(nbytes / (t_m * 1e-3) / 1e9, 1),
+                                  "frac": round(nbytes / (t_m * 1e-3) / 1e9 / peak, 4), "peak_source": src,
+                                  "tflops": round(flops / (t_m * 1e-3) / 1e12, 2)}), flush=True)
+            cop.close()
+
+
 def run_batched(args):
     """Uneven batch of coarse solves (coarse 4^4 / 6^4 / 8^4, nv 8 / 16 / 24, 1-12 right-hand sides
     each, m0 in [-0.44, -0.38]): the lockstep engine vs the single-operator path on the same inputs."""
@@ -470,11 +521,16 @@ def main():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--fp64-baseline-steps", type=int, default=2,
                     help="plain FP64 GMRES(50) solves timed for the speedup (0 = skip)")
+    ap.add_argument("--mrhs", action="store_true",
+                    help="time the multi-right-hand-side tensor-core apply against the per-column path")
     ap.add_argument("--batched", type=int, default=0,
                     help="time the lockstep batched engine on this many uneven operators")
     args = ap.parse_args()
     if args.batched:
         run_batched(args)
+        return
+    if args.mrhs:
+        run_mrhs(args)
         return
     if args.apply_only:
         run_apply_only(args)

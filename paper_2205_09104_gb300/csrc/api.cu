@@ -63,6 +63,7 @@ void free_op(coarse_op* op) {
     delete op->adj_solver[p];
     if (op->blk[p].ptr) cudaFree(op->blk[p].ptr);
   }
+  if (op->mrhs.ptr) cudaFree(op->mrhs.ptr);
   if (op->nb) cudaFree(op->nb);
   if (op->work64) cudaFree(op->work64);
   if (op->red) cudaFree(op->red);
@@ -97,6 +98,7 @@ int ingest(coarse_op* op, const void* self_b, const void* hop_b, uint32_t flags,
   }
   TRY(launch_ingest((const double2*)self_b, (const double2*)hop_b, gamma5_only, op->V, op->n, op->nb,
                     op->blk[0].ptr, op->blk[1].ptr, op->blk[2].ptr, s));
+  TRY(launch_pack_mrhs(op, s));
   COARSE_CUDA(cudaStreamSynchronize(s));
   return COARSE_OK;
 }
@@ -262,6 +264,10 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
     if (!(op->precisions & (1u << p))) continue;
     op->blk[p].bytes = nblk * esz[p];
     CREATE_TRY(dmalloc((char**)&op->blk[p].ptr, op->blk[p].bytes));
+  }
+  if ((op->precisions & (1u << COARSE_PREC_BF16)) && op->max_nrhs > 1) {
+    op->mrhs.bytes = nblk * sizeof(cbf16);
+    CREATE_TRY(dmalloc((char**)&op->mrhs.ptr, op->mrhs.bytes));
   }
   CREATE_TRY(dmalloc(&op->work64, 3 * N * sizeof(double2)));
   CREATE_TRY(dmalloc((char**)&op->apply_scratch, 5 * N * sizeof(double2)));

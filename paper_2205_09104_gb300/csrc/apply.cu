@@ -19,6 +19,18 @@
 #include "batch.cuh"
 
 namespace coarse {
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
 namespace {
 
 template <int N, class BT, class VT, class AC>
@@ -311,16 +323,6 @@ int launch_t(int n, const ApplyArgs& a, cudaStream_t s) {
   return COARSE_OK;
 }
 
-int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
 
 template <int N, class BT>
 int launch_tma_n(const ApplyArgs& a, cudaStream_t s) {

@@ -49,6 +49,7 @@ struct __align__(4) cbf16 { __nv_bfloat16 x, y; };
 // ------------------------------------------------------------------ error state
 void set_error(const char* fmt, ...);
 void note_launch();          // counts kernels launched by the library
+int sm_count();              // multiprocessors of the current device (cached)
 long long launches_so_far();
 int cuda_fail(cudaError_t e, const char* what);
 #define COARSE_CUDA(call)                                      \
@@ -78,6 +79,7 @@ struct coarse_op {
   uint32_t precisions;
   int* nb = nullptr;                // device int32 [V][8]
   coarse::Blocks blk[3];            // FP64, FP32, BF16 copies
+  coarse::Blocks mrhs;              // BF16 blocks in the tensor-core fragment layout (BF16 and max_nrhs > 1)
   coarse::Solver* solver[3] = {nullptr, nullptr, nullptr};
   coarse::Solver* adj_solver[3] = {nullptr, nullptr, nullptr};  // sigma3 D_c(-mu) sigma3 for mu != 0
   double2* work64 = nullptr;        // 3 FP64 work vectors of V*n: residual, generator scratch, sigma3 temp
@@ -144,6 +146,7 @@ inline ApplyArgs make_apply_args(const coarse_op* op, int prec, const void* x, v
   return a;
 }
 int launch_apply_mrhs_bf16(const coarse_op* op, const void* x, void* y, int nrhs, int adjoint, cudaStream_t s);
+int launch_pack_mrhs(const coarse_op* op, cudaStream_t s);  // refresh op->mrhs from the BF16 blocks
 
 // ------------------------------------------------------------------ BLAS kernels
 // Vectors of the solver: complex64 (float2) or complex128 (double2), length N.

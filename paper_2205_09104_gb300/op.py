@@ -88,9 +88,17 @@ class CoarseOp:
         check(lib().coarse_op_update(self.handle, _ptr(self_blocks), _ptr(hop_blocks), _stream(stream)))
 
     # -- ABI calls
-    def apply(self, x: torch.Tensor, precision: int = _abi.PREC_FP64, adjoint: bool = False, stream=None):
+    def apply(self, x: torch.Tensor, precision: int = _abi.PREC_FP64, adjoint: bool = False, stream=None,
+              out: torch.Tensor = None):
+        """y = D_c x (or D_c^H x); x is (N,) or (nrhs, N) on this operator's device.  With BF16 and
+        nrhs > 1 the columns go through the tensor-core multi-right-hand-side kernel."""
         x, nrhs = self._vec(x, _PREC_DT[precision])
-        y = torch.empty_like(x)
+        if out is None:
+            y = torch.empty_like(x)
+        else:
+            if out.shape != x.shape or out.dtype != x.dtype or not out.is_contiguous() or out.device != x.device:
+                raise ValueError("out must be a contiguous tensor of the shape, dtype and device of x")
+            y = out
         fn = lib().coarse_apply_adjoint if adjoint else lib().coarse_apply
         check(fn(self.handle, _ptr(x), _ptr(y), nrhs, precision, _stream(stream)))
         return y
