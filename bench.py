@@ -424,28 +424,33 @@ def run_mrhs(args):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    for L in (4, 6, 8):
-        for nv in (8, 16, 24):
-            op = build_coarse_operator((6, L, nv), (2 * L,) * 4, nv, -0.42, CSW, device=dev)
-            cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(cg.PREC_BF16,),
-                              max_nrhs=12)
-            del op
-            n, V = 2 * nv, cop.V
-            N = n * V
-            for nrhs in (1, 2, 4, 8, 12):
-                X = torch.randn(nrhs, N, dtype=torch.complex64, generator=g).to(dev)
-                Y = torch.empty_like(X)
-                t_m = timed(lambda: cop.apply(X, precision=cg.PREC_BF16, out=Y))
-                t_c = timed(lambda: [cop.apply(X[c], precision=cg.PREC_BF16, out=Y[c]) for c in range(nrhs)])
-                nbytes = 5 * n * n * 4 * V + 2 * nrhs * N * 8
-                flops = 9 * n * n * 8 * V * nrhs
-                print(json.dumps({"mode": "mrhs", "coarse": f"{L}^4", "V": V, "n": n, "nrhs": nrhs,
-                                  "us_mrhs": round(t_m * 1e3, 2), "us_per_column_path": round(t_c * 1e3, 2),
-                                  "speedup": round(t_c / t_m, 2),
-                                  "achieved_gbs": round(nbytes / (t_m * 1e-3) / 1e9, 1),
-                                  "frac": round(nbytes / (t_m * 1e-3) / 1e9 / peak, 4), "peak_source": src,
-                                  "tflops": round(flops / (t_m * 1e-3) / 1e12, 2)}), flush=True)
-            cop.close()
+    cases = [(L, nv, (1, 2, 4, 8, 12)) for L in (4, 6, 8) for nv in (8, 16, 24)]
+    if args.mrhs_case:
+        L, nv, nr = (int(v) for v in args.mrhs_case.split(","))
+        cases = [(L, nv, (nr,))]
+    for L, nv, counts in cases:
+        op = build_coarse_operator((6, L, nv), (2 * L,) * 4, nv, -0.42, CSW, device=dev)
+        cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(cg.PREC_BF16,),
+                          max_nrhs=12)
+        del op
+        torch.cuda.empty_cache()
+        n, V = 2 * nv, cop.V
+        N = n * V
+        for nrhs in counts:
+            X = torch.randn(nrhs, N, dtype=torch.complex64, generator=g).to(dev)
+            Y = torch.empty_like(X)
+            t_m = timed(lambda: cop.apply(X, precision=cg.PREC_BF16, out=Y))
+            t_c = timed(lambda: [cop.apply(X[c], precision=cg.PREC_BF16, out=Y[c]) for c in range(nrhs)])
+            nbytes = 5 * n * n * 4 * V + 2 * nrhs * N * 8
+            flops = 9 * n * n * 8 * V * nrhs
+            print(json.dumps({"mode": "mrhs", "coarse": f"{L}^4", "V": V, "n": n, "nrhs": nrhs,
+                              "us_mrhs": round(t_m * 1e3, 2), "us_per_column_path": round(t_c * 1e3, 2),
+                              "speedup": round(t_c / t_m, 2),
+                              "achieved_gbs": round(nbytes / (t_m * 1e-3) / 1e9, 1),
+                              "frac": round(nbytes / (t_m * 1e-3) / 1e9 / peak, 4), "peak_source": src,
+                              "tflops": round(flops / (t_m * 1e-3) / 1e12, 2)}), flush=True)
+        cop.close()
+    print(json.dumps({"mode": "mrhs-autotune", "decisions": cg.autotune_report().strip().split("\n")}), flush=True)
 
 
 def run_batched(args):
@@ -523,6 +528,8 @@ def main():
                     help="plain FP64 GMRES(50) solves timed for the speedup (0 = skip)")
     ap.add_argument("--mrhs", action="store_true",
                     help="time the multi-right-hand-side tensor-core apply against the per-column path")
+    ap.add_argument("--mrhs-case", default="",
+                    help="one multi-right-hand-side case 'L,nv,nrhs' (coarse L^4, n = 2 nv)")
     ap.add_argument("--batched", type=int, default=0,
                     help="time the lockstep batched engine on this many uneven operators")
     args = ap.parse_args()

@@ -104,7 +104,11 @@ void coarse_op_destroy(coarse_op* op);
  * nrhs : 1 .. desc.max_nrhs.  nrhs > 1 with COARSE_PREC_BF16 runs the
  *        tensor-core multi-right-hand-side kernel.
  * Asynchronous on `stream`.  The requested precision must have been enabled
- * in desc.precisions (FP64 is always available).
+ * in desc.precisions (FP64 is always available).  The FP32 / BF16 kernels
+ * stage data through shared memory with bounded waits; if one ran out, that
+ * launch's y is incomplete and the next synchronising call on the operator
+ * (coarse_residual, coarse_solve, coarse_solve_adjoint, coarse_solve_batched)
+ * returns COARSE_ERR_TIMEOUT and clears the condition.
  */
 int coarse_apply(const coarse_op* op, const void* x, void* y, int nrhs, int precision, void* stream);
 
@@ -233,6 +237,19 @@ int coarse_block_grad(const coarse_op* op, const void* lambda, const void* x, vo
  * (re, im pairs); *d receives the degree (0 if none is built).
  */
 int coarse_op_poly(const coarse_op* op, int precision, double* theta_host, int cap, int* d);
+
+/*
+ * coarse_autotune_report -- the launch autotuner's decisions as text, one line per
+ * kernel family and shape: "<key> -> <config> <microseconds> | <candidates timed>".
+ * The paper has no counterpart: its kernels have a fixed launch shape.  The first
+ * call of a kernel for a new shape times each candidate configuration on the
+ * caller's stream (synchronising it) and keeps the fastest; a stream that is being
+ * captured into a CUDA graph is never timed (the default configuration runs).  If
+ * the environment variable COARSE_AUTOTUNE_CACHE names a file, decisions are read
+ * from it at first use and new ones appended.
+ * buf : host char[len]; receives a NUL-terminated (possibly truncated) report.
+ */
+int coarse_autotune_report(char* buf, long long len);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* coarse_last_error(void);

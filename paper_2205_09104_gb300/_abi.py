@@ -20,7 +20,8 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED"
 # every symbol the header declares
 EXPORTS = ["coarse_op_create", "coarse_op_update", "coarse_op_destroy", "coarse_apply", "coarse_apply_adjoint",
            "coarse_residual", "coarse_solve", "coarse_solve_adjoint", "coarse_solve_batched", "coarse_block_grad",
-           "coarse_op_poly", "coarse_last_error", "coarse_version", "coarse_residual_noalloc"]
+           "coarse_op_poly", "coarse_last_error", "coarse_version", "coarse_residual_noalloc",
+           "coarse_autotune_report"]
 
 
 class CoarseError(RuntimeError):
@@ -78,6 +79,7 @@ def lib() -> ctypes.CDLL:
     L.coarse_solve_batched.argtypes = [P(vp), i32, P(vp), P(vp), P(i32), P(SolveParams), P(SolveInfo), vp]
     L.coarse_block_grad.argtypes = [vp, vp, vp, vp, vp, vp]
     L.coarse_op_poly.argtypes = [vp, i32, P(dbl), i32, P(i32)]
+    L.coarse_autotune_report.argtypes = [ctypes.c_char_p, ctypes.c_longlong]
     L.coarse_last_error.restype = ctypes.c_char_p
     L.coarse_version.restype = ctypes.c_char_p
     for name in EXPORTS:

@@ -64,6 +64,7 @@ void free_op(coarse_op* op) {
     if (op->blk[p].ptr) cudaFree(op->blk[p].ptr);
   }
   if (op->mrhs.ptr) cudaFree(op->mrhs.ptr);
+  if (op->mrhs_x.ptr) cudaFree(op->mrhs_x.ptr);
   if (op->nb) cudaFree(op->nb);
   if (op->work64) cudaFree(op->work64);
   if (op->red) cudaFree(op->red);
@@ -160,6 +161,22 @@ int apply_impl(const coarse_op* op, const void* x, void* y, int nrhs, int precis
   return COARSE_OK;
 }
 
+}  // namespace
+
+// Error flag of the operator's staged stencil kernels (raised when one of their bounded waits ran
+// out, leaving that launch's output incomplete): read and clear it; COARSE_ERR_TIMEOUT if raised.
+int take_stencil_flag(const coarse_op* op, cudaStream_t s) {
+  int h = 0;
+  COARSE_CUDA(cudaMemcpyAsync(&h, op->apply_cnt + op->V, sizeof(int), cudaMemcpyDeviceToHost, s));
+  COARSE_CUDA(cudaStreamSynchronize(s));
+  if (h == 0) return COARSE_OK;
+  COARSE_CUDA(cudaMemsetAsync(op->apply_cnt + op->V, 0, sizeof(int), s));
+  set_error("a bounded wait of a staged stencil kernel ran out; the results since the last check are invalid");
+  return COARSE_ERR_TIMEOUT;
+}
+
+namespace {
+
 int solve_impl(coarse_op* op, const void* b, void* x, int nrhs, const coarse_solve_params* p,
                coarse_solve_info* info, void* stream, int adjoint) {
   TRY(validate_solve(op, b, x, nrhs, p));
@@ -188,6 +205,7 @@ int solve_impl(coarse_op* op, const void* b, void* x, int nrhs, const coarse_sol
     if (rc != COARSE_OK && rc != COARSE_ERR_NOT_CONVERGED) return rc;
     if (rc != COARSE_OK) worst = rc;
   }
+  TRY(take_stencil_flag(op, s));
   return worst;
 }
 
@@ -268,6 +286,8 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
   if ((op->precisions & (1u << COARSE_PREC_BF16)) && op->max_nrhs > 1) {
     op->mrhs.bytes = nblk * sizeof(cbf16);
     CREATE_TRY(dmalloc((char**)&op->mrhs.ptr, op->mrhs.bytes));
+    op->mrhs_x.bytes = 12 * N * sizeof(cbf16);
+    CREATE_TRY(dmalloc((char**)&op->mrhs_x.ptr, op->mrhs_x.bytes));
   }
   CREATE_TRY(dmalloc(&op->work64, 3 * N * sizeof(double2)));
   CREATE_TRY(dmalloc((char**)&op->apply_scratch, 5 * N * sizeof(double2)));
@@ -334,7 +354,7 @@ int coarse_residual(const coarse_op* op, const void* b, const void* x, void* r, 
   COARSE_CUDA(cudaStreamSynchronize(s));
   norms_host[0] = sqrt(h[0]);
   norms_host[1] = sqrt(h[1]);
-  return COARSE_OK;
+  return take_stencil_flag(op, s);
 }
 
 int coarse_solve(coarse_op* op, const void* b, void* x, int nrhs, const coarse_solve_params* params,

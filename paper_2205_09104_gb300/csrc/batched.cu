@@ -589,6 +589,7 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
     }
   }
   if (infos) memcpy(infos, inf.data(), sizeof(coarse_solve_info) * ns);
+  for (int i = 0; i < nops; ++i) TRY(take_stencil_flag(ops[i], s));
   if (worst == COARSE_ERR_NOT_CONVERGED) set_error("coarse_solve_batched: some solves missed the tolerance");
   if (worst == COARSE_ERR_NONFINITE) set_error("coarse_solve_batched: non-finite values in some solves");
   (void)any_nonfinite;

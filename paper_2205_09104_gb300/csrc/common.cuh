@@ -80,6 +80,7 @@ struct coarse_op {
   int* nb = nullptr;                // device int32 [V][8]
   coarse::Blocks blk[3];            // FP64, FP32, BF16 copies
   coarse::Blocks mrhs;              // BF16 blocks in the tensor-core fragment layout (BF16 and max_nrhs > 1)
+  coarse::Blocks mrhs_x;            // 12 columns of BF16 vector fragments (scratch of the multi-RHS apply)
   coarse::Solver* solver[3] = {nullptr, nullptr, nullptr};
   coarse::Solver* adj_solver[3] = {nullptr, nullptr, nullptr};  // sigma3 D_c(-mu) sigma3 for mu != 0
   double2* work64 = nullptr;        // 3 FP64 work vectors of V*n: residual, generator scratch, sigma3 temp
@@ -147,6 +148,8 @@ inline ApplyArgs make_apply_args(const coarse_op* op, int prec, const void* x, v
 }
 int launch_apply_mrhs_bf16(const coarse_op* op, const void* x, void* y, int nrhs, int adjoint, cudaStream_t s);
 int launch_pack_mrhs(const coarse_op* op, cudaStream_t s);  // refresh op->mrhs from the BF16 blocks
+// Reads and clears the operator's stencil error flag (synchronises s); COARSE_ERR_TIMEOUT if raised.
+int take_stencil_flag(const coarse_op* op, cudaStream_t s);
 
 // ------------------------------------------------------------------ BLAS kernels
 // Vectors of the solver: complex64 (float2) or complex128 (double2), length N.

@@ -15,8 +15,8 @@
 //   word index ((((x*5 + b)*NT + ti)*NT + tk)*2 + p)*128 + lane*4 + w,   NT = n/16,
 //   lane = 4g + t, word w holds plane p (0 re, 1 im) of F[16ti + g + 8(w&1)][16tk + 2t + 8(w>>1) + {0,1}]
 // which is exactly the lane's m16n8k16 A fragment {a0, a1, a2, a3} of tile (ti, tk): one 16-byte
-// coalesced load per lane per tile and plane.  The transpose F^T of a tile is made in registers
-// with movmatrix (a0' = T(a0), a1' = T(a2), a2' = T(a1), a3' = T(a3)).
+// load per lane per tile and plane, conflict-free from shared memory.  The transpose F^T of a
+// tile is made in registers with movmatrix (a0' = T(a0), a1' = T(a2), a2' = T(a1), a3' = T(a3)).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -27,6 +27,7 @@ namespace coarse {
 
 constexpr int kMrhsTile = 4;    // columns per tensor-core tile (B operand is 8 wide: re, im of 4 columns)
 constexpr int kMrhsMaxT = 3;    // tiles per pass: up to 12 columns
+constexpr int kMrhsPass = kMrhsTile * kMrhsMaxT;
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint4& a, uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -52,111 +53,83 @@ __device__ __forceinline__ uint32_t bf2_bits(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// Where the columns of one pass live: column q of the pass is x + q * ldx (complex64 elements).
-struct MrhsCols {
-  const float2* x;
-  float2* y;
-  long long ldx, ldy;
-  int R;  // columns in this pass (1..12)
+// Accumulators of one warp: output rows 16rt .. 16rt+15, T column tiles.
+template <int T>
+struct MrhsAcc {
+  float P1[T][4], P2[T][4], Q1[T][4], Q2[T][4];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int tl = 0; tl < T; ++tl)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) P1[tl][i] = P2[tl][i] = Q1[tl][i] = Q2[tl][i] = 0.f;
+  }
 };
 
-// B fragments of vector site s, k tile kt, column tile tl: lane (g, t) feeds column 4tl + g/2,
-// real (g even) or imaginary (g odd) part, of entries 16kt + 2t + {0, 1} (b0) and + 8 (b1).
-// neg_lo / neg_hi: flip the sign of the entries of the first / second half of the k tile.
-template <int N>
-__device__ __forceinline__ void mrhs_bfrag(const MrhsCols& c, int s, int kt, int tl, uint32_t neg_lo,
-                                           uint32_t neg_hi, uint32_t& b0, uint32_t& b1) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int q = kMrhsTile * tl + (g >> 1);
-  if (q >= c.R) { b0 = b1 = 0u; return; }
-  const float4* p = reinterpret_cast<const float4*>(c.x + q * c.ldx + (size_t)s * N + 16 * kt + 2 * t);
-  const float4 lo = __ldg(p), hi = __ldg(p + 4);
-  b0 = ((g & 1) ? bf2_bits(lo.y, lo.w) : bf2_bits(lo.x, lo.z)) ^ neg_lo;
-  b1 = ((g & 1) ? bf2_bits(hi.y, hi.w) : bf2_bits(hi.x, hi.z)) ^ neg_hi;
+// Fragment-native BF16 vectors (built by k_pack_mrhs_x from the complex64 columns): for each
+// site, column tile tl and k tile kt, lane (g, t) holds the two B-fragment registers
+//   b0 = part (g & 1 ? Im : Re) of x_{4tl + g/2}[16kt + 2t + {0, 1}],   b1 = the same at + 8,
+// as one uint2 at index (tl * NT + kt) * 32 + lane; columns >= R hold zeros.  One site of T tiles
+// is T * NT * 256 bytes, contiguous.
+__device__ __forceinline__ uint32_t s3mask(int k0, int nv) { return k0 < nv ? 0u : 0x80008000u; }
+
+// One staged block (all NT x NT tiles, fragment layout) times the staged vectors of its source site.
+// Forward / self blocks (bwd = 0): P += F w with w = (adj ? s3 x : x), rows of tile rt.
+// Backward blocks (bwd = 1): Q += F^T-products on (adj ? x : s3 x), columns of tile rt (F^H w).
+template <int N, int T>
+__device__ __forceinline__ void mrhs_block(const uint4* blk, const uint2* vec, int rt, int bwd, int adj,
+                                           MrhsAcc<T>& acc) {
+  constexpr int NT = N / 16;
+  const int lane = threadIdx.x & 31;
+  const int flip = bwd ? !adj : adj;  // sigma3 on the B operand
+#pragma unroll
+  for (int kt = 0; kt < NT; ++kt) {
+    uint4 are, aim;
+    if (!bwd) {
+      are = blk[((rt * NT + kt) * 2 + 0) * 32 + lane];
+      aim = blk[((rt * NT + kt) * 2 + 1) * 32 + lane];
+    } else {
+      are = frag_transpose(blk[((kt * NT + rt) * 2 + 0) * 32 + lane]);
+      aim = frag_transpose(blk[((kt * NT + rt) * 2 + 1) * 32 + lane]);
+    }
+    const uint32_t nl = flip ? s3mask(16 * kt, N / 2) : 0u, nh = flip ? s3mask(16 * kt + 8, N / 2) : 0u;
+#pragma unroll
+    for (int tl = 0; tl < T; ++tl) {
+      const uint2 bv = vec[(tl * NT + kt) * 32 + lane];
+      const uint32_t b0 = bv.x ^ nl, b1 = bv.y ^ nh;
+      if (!bwd) {
+        mma_bf16(acc.P1[tl], are, b0, b1);
+        mma_bf16(acc.P2[tl], aim, b0, b1);
+      } else {
+        mma_bf16(acc.Q1[tl], are, b0, b1);
+        mma_bf16(acc.Q2[tl], aim, b0, b1);
+      }
+    }
+  }
 }
 
-// One warp computes output rows 16rt .. 16rt+15 of site x for all columns of the pass.
-//   y_q[x] = o (P + s3 Q + i mu' v),  P = A_x w_x + sum_mu F_{x,mu} w_{x+mu},
-//   Q = sum_mu F_{x-mu,mu}^H (s3 w_{x-mu}),  w = (adj ? s3 x : x),  v = (adj ? x : s3 x),
-//   o = (adj ? s3 : 1), mu' = adj ? -mu : mu (passed in already signed).
-// adj = 1 gives D^H = s3 D(-mu) s3 (gamma5-hermiticity, Sec. 2).
+// Output rows r0 = 16rt + g and r1 = r0 + 8 of column q = 4tl + t:
+//   y = o (P + s3 Q + i mu' v),  v = (adj ? x : s3 x),  o = (adj ? s3 : 1),
+// with mu' already signed (-mu for the adjoint).  Returns the two complex values.
 template <int N, int T>
-__device__ __forceinline__ void mrhs_rows(const uint4* __restrict__ frag, const int* __restrict__ nb,
-                                          const MrhsCols& c, int x, int rt, float mu, int adj) {
-  constexpr int NT = N / 16, NV = N / 2;
-  constexpr size_t TILE = 2 * 32;  // uint4 per tile (two planes)
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float P1[T][4], P2[T][4], Q1[T][4], Q2[T][4];
-#pragma unroll
-  for (int tl = 0; tl < T; ++tl)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) P1[tl][i] = P2[tl][i] = Q1[tl][i] = Q2[tl][i] = 0.f;
-  // sign masks of sigma3 per half k tile (NV is a multiple of 8, so uniform over the warp)
-  auto s3mask = [](int k0) -> uint32_t { return k0 < NV ? 0u : 0x80008000u; };
-
-  // ---- pull: self block and forward hops
-#pragma unroll 1
-  for (int b = 0; b < 5; ++b) {
-    const int s = b == 0 ? x : __ldg(nb + x * 8 + (b - 1));
-    const uint4* base = frag + (((size_t)x * 5 + b) * NT + rt) * NT * TILE;
-#pragma unroll
-    for (int kt = 0; kt < NT; ++kt) {
-      const uint4 are = __ldg(base + kt * TILE + lane);
-      const uint4 aim = __ldg(base + kt * TILE + 32 + lane);
-      const uint32_t nl = adj ? s3mask(16 * kt) : 0u, nh = adj ? s3mask(16 * kt + 8) : 0u;
-#pragma unroll
-      for (int tl = 0; tl < T; ++tl) {
-        uint32_t b0, b1;
-        mrhs_bfrag<N>(c, s, kt, tl, nl, nh, b0, b1);
-        mma_bf16(P1[tl], are, b0, b1);
-        mma_bf16(P2[tl], aim, b0, b1);
-      }
-    }
-  }
-  // ---- backward hops: blocks of the neighbours x - mu, transposed in registers
-#pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {
-    const int s = __ldg(nb + x * 8 + 4 + mu);
-#pragma unroll
-    for (int kt = 0; kt < NT; ++kt) {
-      const uint4* base = frag + ((((size_t)s * 5 + 1 + mu) * NT + kt) * NT + rt) * TILE;
-      const uint4 are = frag_transpose(__ldg(base + lane));
-      const uint4 aim = frag_transpose(__ldg(base + 32 + lane));
-      const uint32_t nl = adj ? 0u : s3mask(16 * kt), nh = adj ? 0u : s3mask(16 * kt + 8);
-#pragma unroll
-      for (int tl = 0; tl < T; ++tl) {
-        uint32_t b0, b1;
-        mrhs_bfrag<N>(c, s, kt, tl, nl, nh, b0, b1);
-        mma_bf16(Q1[tl], are, b0, b1);
-        mma_bf16(Q2[tl], aim, b0, b1);
-      }
-    }
-  }
-  // ---- epilogue: lane (g, t) owns rows r0 = 16rt + g, r1 = r0 + 8 of column 4tl + t
-  const int r0 = 16 * rt + g, r1 = r0 + 8;
+__device__ __forceinline__ void mrhs_rows_out(const MrhsAcc<T>& acc, int tl, int rt, const float2* xsite, float mu,
+                                              int adj, float2& y0, float2& y1) {
+  constexpr int NV = N / 2;
+  const int g = (threadIdx.x & 31) >> 2;
   const float s0 = (16 * rt < NV) ? 1.f : -1.f, s1 = (16 * rt + 8 < NV) ? 1.f : -1.f;
-#pragma unroll
-  for (int tl = 0; tl < T; ++tl) {
-    const int q = kMrhsTile * tl + t;
-    if (q >= c.R) continue;
-    float2 y0 = make_float2(P1[tl][0] - P2[tl][1] + s0 * (Q1[tl][0] + Q2[tl][1]),
-                            P1[tl][1] + P2[tl][0] + s0 * (Q1[tl][1] - Q2[tl][0]));
-    float2 y1 = make_float2(P1[tl][2] - P2[tl][3] + s1 * (Q1[tl][2] + Q2[tl][3]),
-                            P1[tl][3] + P2[tl][2] + s1 * (Q1[tl][3] - Q2[tl][2]));
-    if (mu != 0.f) {
-      const float2* xs = c.x + q * c.ldx + (size_t)x * N;
-      const float2 v0 = __ldg(xs + r0), v1 = __ldg(xs + r1);
-      const float m0 = adj ? mu : mu * s0, m1 = adj ? mu : mu * s1;
-      y0.x -= m0 * v0.y; y0.y += m0 * v0.x;
-      y1.x -= m1 * v1.y; y1.y += m1 * v1.x;
-    }
-    if (adj) {
-      y0.x *= s0; y0.y *= s0;
-      y1.x *= s1; y1.y *= s1;
-    }
-    float2* ys = c.y + q * c.ldy + (size_t)x * N;
-    ys[r0] = y0;
-    ys[r1] = y1;
+  y0 = make_float2(acc.P1[tl][0] - acc.P2[tl][1] + s0 * (acc.Q1[tl][0] + acc.Q2[tl][1]),
+                   acc.P1[tl][1] + acc.P2[tl][0] + s0 * (acc.Q1[tl][1] - acc.Q2[tl][0]));
+  y1 = make_float2(acc.P1[tl][2] - acc.P2[tl][3] + s1 * (acc.Q1[tl][2] + acc.Q2[tl][3]),
+                   acc.P1[tl][3] + acc.P2[tl][2] + s1 * (acc.Q1[tl][3] - acc.Q2[tl][2]));
+  if (mu != 0.f) {
+    const int r0 = 16 * rt + g;
+    const float2 v0 = __ldg(xsite + r0), v1 = __ldg(xsite + r0 + 8);
+    const float m0 = adj ? mu : mu * s0, m1 = adj ? mu : mu * s1;
+    y0.x -= m0 * v0.y; y0.y += m0 * v0.x;
+    y1.x -= m1 * v1.y; y1.y += m1 * v1.x;
+  }
+  if (adj) {
+    y0.x *= s0; y0.y *= s0;
+    y1.x *= s1; y1.y *= s1;
   }
 }
 

@@ -173,3 +173,10 @@ class CoarseSolve(torch.autograd.Function):
         if ctx.needs_input_grad[1] or ctx.needs_input_grad[2]:
             gs, gh = ctx.op.block_grad(lam, x)
         return lam, gs, gh, None, None
+
+
+def autotune_report() -> str:
+    """Decisions of the library's launch autotuner (one line per kernel family and shape)."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(lib().coarse_autotune_report(buf, len(buf)))
+    return buf.value.decode()
