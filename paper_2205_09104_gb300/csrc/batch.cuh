@@ -111,6 +111,34 @@ __device__ inline void* bsel(const BSolve& s, int sel, int step) {
 }
 
 int launch_bapply(int prec, int n, const BApply& a, cudaStream_t s);
+
+// ---- multi-RHS (tensor-core) stencil phases: every column of one operator in one pass
+struct BMOp {
+  const void* frag;    // fragment-native BF16 blocks (coarse_op::mrhs)
+  const int* nb;
+  void* xb;            // packed BF16 B fragments of the phase's input columns, [V][T][NT][32] uint2
+  int V, n, R, T;      // sites, dof per site, columns (solves), column tiles ceil(R/4)
+  int s0;              // first solve of the operator (its columns are s0 .. s0 + R - 1)
+  float mu;
+};
+
+struct BMApply {
+  const BSolve* S;
+  const BMOp* ops;
+  const int* idx;       // operators of this n-group (count)
+  const int* grp_off;   // prefix sums of their site groups of P sites (count + 1)
+  int count;
+  int total_groups;
+  int mode, xsel, ysel, coef_off, gate;
+  const int* step;
+  int* err;             // raised if a bounded wait of the pipeline expired
+};
+
+// packs the input columns (BSel xsel, gated) of all operators; word_off = prefix sums over the
+// operators of their packed words (nops + 1 entries)
+int launch_bpack_mrhs(const BMApply& a, int nops, const int* word_off, int total_words, cudaStream_t s);
+// the stencil phase of one n-group; P sites per stage, S stages
+int launch_bapply_mrhs(int n, int P, int S, const BMApply& a, cudaStream_t s);
 int launch_bapply64_residual(int n, const BApply& a, cudaStream_t s);
 
 // chunked Gram-Schmidt / vector phases over all solves

@@ -17,6 +17,7 @@
 
 #include "batch.cuh"
 #include "common.cuh"
+#include "mrhs_core.cuh"
 #include "solver.cuh"
 
 namespace coarse {
@@ -40,8 +41,28 @@ struct Group {
   int* site_off = nullptr;
 };
 
+// n-group of the multi-RHS stencil phases
+struct MGroup {
+  int n = 0, P = 1, S = 3;
+  BMApply a{};  // operator list, site-group offsets (device); phase fields filled per launch
+};
+
+// sites per stage and pipeline stages of the batched multi-RHS kernel per n (the standalone
+// kernel's autotuned choices on 4^4 .. 8^4 lattices)
+inline void bm_shape(int n, int* P, int* S) {
+  *P = n == 48 ? 1 : 2;
+  *S = n == 16 ? 5 : 3;
+}
+
 struct Batch {
   int prec = COARSE_PREC_FP32;
+  bool mrhs = false;              // BF16 stencil phases on the tensor-core multi-RHS kernel
+  std::vector<MGroup> mgroups;
+  BMOp* dops = nullptr;
+  int nops = 0;
+  int* word_off = nullptr;
+  int total_words = 0;
+  int* merr = nullptr;
   int m = 0, dd = 0, ns = 0, E = 4, total_chunks = 0, steps_max = 0;
   bool any_kc = false;
   char* mem = nullptr;
@@ -71,6 +92,19 @@ struct Batch {
 
   // one stencil phase over all n-groups
   int apply_phase(int mode, int xsel, int ysel, int coef_off, int gate, cudaStream_t s) {
+    if (mrhs) {
+      for (size_t i = 0; i < mgroups.size(); ++i) {
+        BMApply a = mgroups[i].a;
+        a.mode = mode;
+        a.xsel = xsel;
+        a.ysel = ysel;
+        a.coef_off = coef_off;
+        a.gate = gate;
+        if (i == 0) TRY(launch_bpack_mrhs(a, nops, word_off, total_words, s));
+        TRY(launch_bapply_mrhs(mgroups[i].n, mgroups[i].P, mgroups[i].S, a, s));
+      }
+      return COARSE_OK;
+    }
     for (const Group& g : groups) {
       BApply a;
       a.S = dS;
@@ -255,6 +289,20 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   const size_t o_S = take(sizeof(BSolve) * ns);
   const size_t o_coff = take(sizeof(int) * (ns + 1));
   const size_t o_groups = take(sizeof(int) * (2 * ns + 8) * 3);
+  // multi-RHS stencil phases: BF16 inner solves, every operator carrying the fragment-layout
+  // blocks (created with max_nrhs > 1) and at most 12 columns
+  B.mrhs = prec == COARSE_PREC_BF16;
+  for (int i = 0; i < nops; ++i) B.mrhs = B.mrhs && ops[i]->mrhs.ptr != nullptr && nrhs[i] <= kMrhsColumns;
+  std::vector<size_t> off_xb(nops, 0);
+  size_t o_mops = 0, o_mgrp = 0, o_woff = 0, o_merr = 0;
+  if (B.mrhs) {
+    o_mops = take(sizeof(BMOp) * nops);
+    o_mgrp = take(sizeof(int) * (2 * (size_t)nops + 8) * 3);
+    o_woff = take(sizeof(int) * ((size_t)nops + 1));
+    o_merr = take(64);
+    for (int i = 0; i < nops; ++i)
+      off_xb[i] = take((size_t)ops[i]->V * ((nrhs[i] + 3) / 4) * (ops[i]->n / 16) * 256);
+  }
   {
     int sidx = 0;
     for (int i = 0; i < nops; ++i) {
@@ -401,6 +449,70 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
     }
   }
   COARSE_CUDA(cudaMemcpyAsync(B.dS, hs.data(), sizeof(BSolve) * ns, cudaMemcpyHostToDevice, s));
+  std::vector<BMOp> hops;
+  std::vector<int> woff, mgroup_tab;
+  if (B.mrhs) {
+    hops.resize(nops);
+    woff.assign(nops + 1, 0);
+    int s0 = 0;
+    long long words = 0;
+    for (int i = 0; i < nops; ++i) {
+      BMOp& o = hops[i];
+      o.frag = ops[i]->mrhs.ptr;
+      o.nb = ops[i]->nb;
+      o.xb = B.mem + off_xb[i];
+      o.V = ops[i]->V;
+      o.n = ops[i]->n;
+      o.R = nrhs[i];
+      o.T = (nrhs[i] + 3) / 4;
+      o.s0 = s0;
+      o.mu = (float)ops[i]->mu;
+      s0 += nrhs[i];
+      words += (long long)o.V * o.T * (o.n / 16) * 64;
+      if (words >= (1ll << 31)) {
+        set_error("coarse_solve_batched: %lld packed vector words exceed the 32-bit index", words);
+        return COARSE_ERR_INVALID_ARG;
+      }
+      woff[i + 1] = (int)words;
+    }
+    B.dops = reinterpret_cast<BMOp*>(B.mem + o_mops);
+    B.nops = nops;
+    B.word_off = reinterpret_cast<int*>(B.mem + o_woff);
+    B.total_words = woff[nops];
+    B.merr = reinterpret_cast<int*>(B.mem + o_merr);
+    COARSE_CUDA(cudaMemcpyAsync(B.dops, hops.data(), sizeof(BMOp) * nops, cudaMemcpyHostToDevice, s));
+    COARSE_CUDA(cudaMemcpyAsync(B.word_off, woff.data(), sizeof(int) * (nops + 1), cudaMemcpyHostToDevice, s));
+    // n-groups: operator lists and prefix sums of their site groups
+    mgroup_tab.reserve(2 * (size_t)nops + 8 * 3);
+    std::vector<std::pair<size_t, size_t>> spans;
+    for (int n : {16, 32, 48}) {
+      MGroup mg;
+      mg.n = n;
+      bm_shape(n, &mg.P, &mg.S);
+      std::vector<int> idx, off(1, 0);
+      for (int i = 0; i < nops; ++i)
+        if (hops[i].n == n) {
+          idx.push_back(i);
+          off.push_back(off.back() + (hops[i].V + mg.P - 1) / mg.P);
+        }
+      if (idx.empty()) continue;
+      const size_t at = mgroup_tab.size();
+      mgroup_tab.insert(mgroup_tab.end(), idx.begin(), idx.end());
+      mgroup_tab.insert(mgroup_tab.end(), off.begin(), off.end());
+      int* base = reinterpret_cast<int*>(B.mem + o_mgrp) + at;
+      mg.a.S = B.dS;
+      mg.a.ops = B.dops;
+      mg.a.idx = base;
+      mg.a.grp_off = base + idx.size();
+      mg.a.count = (int)idx.size();
+      mg.a.total_groups = off.back();
+      mg.a.step = B.step;
+      mg.a.err = B.merr;
+      B.mgroups.push_back(mg);
+    }
+    COARSE_CUDA(cudaMemcpyAsync(B.mem + o_mgrp, mgroup_tab.data(), sizeof(int) * mgroup_tab.size(),
+                                cudaMemcpyHostToDevice, s));
+  }
   // n-groups of the stencil phases
   {
     int* g0 = reinterpret_cast<int*>(B.mem + o_groups);
@@ -590,6 +702,14 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   }
   if (infos) memcpy(infos, inf.data(), sizeof(coarse_solve_info) * ns);
   for (int i = 0; i < nops; ++i) TRY(take_stencil_flag(ops[i], s));
+  if (B.mrhs) {
+    int h = 0;
+    COARSE_CUDA(cudaMemcpy(&h, B.merr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+      set_error("coarse_solve_batched: a bounded wait of the multi-RHS stencil ran out; results are invalid");
+      return COARSE_ERR_TIMEOUT;
+    }
+  }
   if (worst == COARSE_ERR_NOT_CONVERGED) set_error("coarse_solve_batched: some solves missed the tolerance");
   if (worst == COARSE_ERR_NONFINITE) set_error("coarse_solve_batched: non-finite values in some solves");
   (void)any_nonfinite;

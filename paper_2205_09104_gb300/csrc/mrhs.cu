@@ -1,22 +1,11 @@
 // Multi-right-hand-side apply Y = D_c X on tensor cores (BF16 blocks and vector fragments,
-// FP32 accumulation), and the repacking of the BF16 blocks into the fragment-native layout
-// it reads.  The per-block tensor-core computation is in mrhs_core.cuh.
-//
-// Staging.  A CTA owns P consecutive sites at a time (P = 4, 2, 1 for n = 16, 32, 48) and walks
-// the 9 blocks of Eq. (6) for them: item b = 0 self, 1..4 forward hop mu = b-1 (block of x, vector
-// of x+mu), 5..8 backward hop mu = b-5 (block of x-mu, vector of x-mu).  A pre-pass
-// (k_pack_mrhs_x) rounds the R complex64 columns to BF16 B fragments, contiguous per site, so
-// that one producer warp brings each item's P blocks and P vector sets into a ring of S
-// shared-memory stages with 2P 1D bulk copies completing on the stage's "full" mbarrier;
-// P * n/16 consumer warps (site p, row tile rt) run the tensor-core products from shared memory
-// and release the stage on its "empty" mbarrier.  Every byte is loaded once per CTA.  All waits
-// are bounded (pipe.cuh): on expiry the kernel raises *err, the producer drains its copies in
-// flight, and all warps return.
+// FP32 accumulation) for one operator, the repacking of its BF16 blocks into the
+// fragment-native layout, and the packing of the vectors into BF16 B fragments.  The pipeline
+// is mrhs_ring.cuh; the per-block tensor-core products are mrhs_core.cuh.
 #include <cstdio>
 #include <vector>
 
-#include "mrhs_core.cuh"
-#include "pipe.cuh"
+#include "mrhs_ring.cuh"
 #include "tune.cuh"
 
 namespace coarse {
@@ -87,131 +76,44 @@ template <int N, int P> struct MrhsShape {
   static constexpr int NT = N / 16;
   static constexpr int WC = P * NT;            // consumer warps
   static constexpr int THREADS = (WC + 1) * 32;
-  static constexpr uint32_t BLK = 4u * N * N;  // bytes of one block
 };
 
-// P sites per stage (template), S stages (runtime); see the file comment.
+// One operator, columns x + q*ldx, plain or adjoint product.
+template <int N, int T>
+struct MrhsPlain {
+  MrhsArgs a;
+  __device__ int ngroups(int P) const { return (a.V + P - 1) / P; }
+  __device__ MrhsGroup group(int g, int P) const {
+    MrhsGroup r;
+    r.frag = a.frag;
+    r.nb = a.nb;
+    r.xb = a.xb;
+    r.V = a.V;
+    r.x0 = g * P;
+    r.np = a.V - r.x0 < P ? a.V - r.x0 : P;
+    r.T = T;
+    r.tag = 0;
+    return r;
+  }
+  __device__ int adjoint() const { return a.adj; }
+  __device__ void finish(const MrhsGroup&, int x, int rt, const MrhsAcc<T>& acc) const {
+    const int lane = threadIdx.x & 31, t = lane & 3, g = lane >> 2;
+#pragma unroll
+    for (int tl = 0; tl < T; ++tl) {
+      const int q = kMrhsTile * tl + t;
+      if (q >= a.R) continue;
+      float2 y0, y1;
+      mrhs_rows_out<N, T>(acc, tl, rt, a.x + q * a.ldx + (size_t)x * N, a.mu, a.adj, y0, y1);
+      float2* ys = a.y + q * a.ldy + (size_t)x * N + 16 * rt + g;
+      ys[0] = y0;
+      ys[8] = y1;
+    }
+  }
+};
+
 template <int N, int T, int P>
 __global__ void __launch_bounds__(MrhsShape<N, P>::THREADS) k_apply_mrhs(MrhsArgs a) {
-  using Sh = MrhsShape<N, P>;
-  constexpr int NT = Sh::NT, WC = Sh::WC;
-  constexpr uint32_t BLK = Sh::BLK, VB = T * NT * 256u;  // bytes of one block / one site's vector fragments
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int S = a.S;
-  const uint32_t SB = a.SB;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB);
-  uint64_t* empty = full + S;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ngroups = (a.V + P - 1) / P;
-  const int my_groups = (int)blockIdx.x < ngroups ? (ngroups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int items = my_groups * 9;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < S; ++i) {
-      mbar_init(full + i, 1);
-      mbar_init(empty + i, WC);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  if (warp == WC) {  // ---------------------------------------------------------- producer
-    // lane p < P issues the block copy of site p of the group, lane P + p its vector copy; both
-    // keep the site's neighbour row (prefetched one group ahead) in registers.
-    const int p = lane < P ? lane : lane - P;
-    const bool active = lane < 2 * P;
-    int4 nb_lo = make_int4(0, 0, 0, 0), nb_hi = nb_lo, nx_lo = nb_lo, nx_hi = nb_lo;
-    auto fetch = [&](int grp, int4& lo, int4& hi) {
-      const int x = grp * P + p;
-      if (active && grp < ngroups && x < a.V) {
-        lo = __ldg(reinterpret_cast<const int4*>(a.nb + x * 8));
-        hi = __ldg(reinterpret_cast<const int4*>(a.nb + x * 8 + 4));
-      }
-    };
-    fetch((int)blockIdx.x, nx_lo, nx_hi);
-    int ok = 1;
-    int it = 0;
-    for (; it < items; ++it) {
-      const int slot = it % S;
-      const int grp = (int)blockIdx.x + (it / 9) * (int)gridDim.x, b = it % 9;
-      if (b == 0) {
-        nb_lo = nx_lo;
-        nb_hi = nx_hi;
-        fetch(grp + (int)gridDim.x, nx_lo, nx_hi);
-      }
-      if (it >= S && lane == 0) ok = mbar_wait_suspend(empty + slot, (uint32_t)((it / S - 1) & 1)) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      const int x0 = grp * P;
-      const int np = a.V - x0 < P ? a.V - x0 : P;
-      unsigned char* st = smem + (size_t)slot * SB;
-      if (lane == 0) mbar_expect_tx(full + slot, (uint32_t)np * (BLK + VB));
-      __syncwarp();
-      if (active && p < np) {
-        const int x = x0 + p;
-        // source site of the vector: x (self), x + mu (forward hop), x - mu (backward hop)
-        int src = x;
-        switch (b) {
-          case 1: src = nb_lo.x; break;
-          case 2: src = nb_lo.y; break;
-          case 3: src = nb_lo.z; break;
-          case 4: src = nb_lo.w; break;
-          case 5: src = nb_hi.x; break;
-          case 6: src = nb_hi.y; break;
-          case 7: src = nb_hi.z; break;
-          case 8: src = nb_hi.w; break;
-        }
-        if (lane < P) {
-          const size_t blkid = b < 5 ? (size_t)x * 5 + b : (size_t)src * 5 + 1 + (b - 5);
-          bulk_g2s(st + p * BLK, a.frag + blkid * (BLK / 16), BLK, full + slot);
-        } else {
-          bulk_g2s(st + P * BLK + p * VB, a.xb + (size_t)src * (VB / 8), VB, full + slot);
-        }
-      }
-    }
-    if (!ok && lane == 0) {
-      atomicExch(a.err, 1);
-      // drain the bulk copies this CTA still has in flight (bounded) before it exits
-      for (int j = it - S < 0 ? 0 : it - S; j < it; ++j) mbar_wait(full + (j % S), (uint32_t)((j / S) & 1));
-    }
-    return;
-  }
-
-  // ---------------------------------------------------------------------------------- consumers
-  const int p = warp / NT, rt = warp % NT;
-  const int t = lane & 3, g = lane >> 2;
-  MrhsAcc<T> acc;
-  acc.zero();
-  int ok = 1;
-  for (int it = 0; it < items; ++it) {
-    const int slot = it % S;
-    if (!mbar_wait_suspend(full + slot, (uint32_t)((it / S) & 1))) ok = 0;
-    if (!__all_sync(0xffffffffu, ok)) break;
-    const int grp = (int)blockIdx.x + (it / 9) * (int)gridDim.x, b = it % 9;
-    const int x = grp * P + p;
-    const bool valid = x < a.V;
-    const unsigned char* st = smem + (size_t)slot * SB;
-    if (valid)
-      mrhs_block<N, T>(reinterpret_cast<const uint4*>(st + p * BLK),
-                       reinterpret_cast<const uint2*>(st + P * BLK + p * VB), rt, b >= 5, a.adj, acc);
-    __syncwarp();
-    if (lane == 0) mbar_arrive(empty + slot);
-    if (b == 8) {
-      if (valid) {
-#pragma unroll
-        for (int tl = 0; tl < T; ++tl) {
-          const int q = kMrhsTile * tl + t;
-          if (q >= a.R) continue;
-          float2 y0, y1;
-          mrhs_rows_out<N, T>(acc, tl, rt, a.x + q * a.ldx + (size_t)x * N, a.mu, a.adj, y0, y1);
-          float2* ys = a.y + q * a.ldy + (size_t)x * N + 16 * rt + g;
-          ys[0] = y0;
-          ys[8] = y1;
-        }
-      }
-      acc.zero();
-    }
-  }
-  if (!ok && lane == 0) atomicExch(a.err, 1);
+  mrhs_ring<N, P, T>(MrhsPlain<N, T>{a}, a.S, a.SB, a.err);
 }
 
 constexpr int kMrhsMaxSmem = 200 * 1024;
@@ -225,7 +127,7 @@ int launch_mrhs_cfg(MrhsArgs a, int S, cudaStream_t s) {
     COARSE_CUDA(cudaFuncSetAttribute(k_apply_mrhs<N, T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMrhsMaxSmem));
     attr = true;
   }
-  a.SB = (uint32_t)P * (Sh::BLK + (uint32_t)T * Sh::NT * 256u);
+  a.SB = mrhs_stage_bytes(N, P, T);
   if (S <= 0) S = (int)((64u * 1024u) / a.SB);
   S = S < 2 ? 2 : (S > 8 ? 8 : S);
   while (S > 2 && (size_t)S * a.SB + 16 * S > (size_t)kMrhsMaxSmem) --S;
