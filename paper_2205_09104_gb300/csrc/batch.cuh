@@ -127,6 +127,7 @@ struct BMApply {
   const BMOp* ops;
   const int* idx;       // operators of this n-group (count)
   const int* grp_off;   // prefix sums of their site groups of P sites (count + 1)
+  const int* grp_op;    // position in idx of the operator of each site group (total_groups)
   int count;
   int total_groups;
   int mode, xsel, ysel, coef_off, gate;

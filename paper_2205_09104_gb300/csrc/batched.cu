@@ -297,7 +297,13 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   size_t o_mops = 0, o_mgrp = 0, o_woff = 0, o_merr = 0;
   if (B.mrhs) {
     o_mops = take(sizeof(BMOp) * nops);
-    o_mgrp = take(sizeof(int) * (2 * (size_t)nops + 8) * 3);
+    size_t groups = 0;
+    for (int i = 0; i < nops; ++i) {
+      int P, S;
+      bm_shape(ops[i]->n, &P, &S);
+      groups += (ops[i]->V + P - 1) / P;
+    }
+    o_mgrp = take(sizeof(int) * ((2 * (size_t)nops + 8) * 3 + groups));
     o_woff = take(sizeof(int) * ((size_t)nops + 1));
     o_merr = take(64);
     for (int i = 0; i < nops; ++i)
@@ -483,7 +489,6 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
     COARSE_CUDA(cudaMemcpyAsync(B.dops, hops.data(), sizeof(BMOp) * nops, cudaMemcpyHostToDevice, s));
     COARSE_CUDA(cudaMemcpyAsync(B.word_off, woff.data(), sizeof(int) * (nops + 1), cudaMemcpyHostToDevice, s));
     // n-groups: operator lists and prefix sums of their site groups
-    mgroup_tab.reserve(2 * (size_t)nops + 8 * 3);
     std::vector<std::pair<size_t, size_t>> spans;
     for (int n : {16, 32, 48}) {
       MGroup mg;
@@ -499,11 +504,14 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
       const size_t at = mgroup_tab.size();
       mgroup_tab.insert(mgroup_tab.end(), idx.begin(), idx.end());
       mgroup_tab.insert(mgroup_tab.end(), off.begin(), off.end());
+      for (size_t k = 0; k < idx.size(); ++k)
+        for (int g = off[k]; g < off[k + 1]; ++g) mgroup_tab.push_back((int)k);
       int* base = reinterpret_cast<int*>(B.mem + o_mgrp) + at;
       mg.a.S = B.dS;
       mg.a.ops = B.dops;
       mg.a.idx = base;
       mg.a.grp_off = base + idx.size();
+      mg.a.grp_op = base + idx.size() + off.size();
       mg.a.count = (int)idx.size();
       mg.a.total_groups = off.back();
       mg.a.step = B.step;

@@ -10,11 +10,13 @@ namespace {
 
 template <int N>
 struct BMrhsPolicy {
-  BMApply a;
-  int step;  // Arnoldi step of the phase (device counter, read once)
-  __device__ int ngroups(int) const { return a.total_groups; }
+  static constexpr bool kRuntimeT = true;
+  const BMApply* pa;  // the kernel's __grid_constant__ parameter
+  int step;           // Arnoldi step of the phase (device counter, read once)
+  __device__ int ngroups(int) const { return pa->total_groups; }
   __device__ MrhsGroup group(int g, int P) const {
-    const int k = find_solve(a.grp_off, a.count, g);
+    const BMApply& a = *pa;
+    const int k = __ldg(a.grp_op + g);
     const BMOp& op = a.ops[a.idx[k]];
     MrhsGroup r;
     r.frag = static_cast<const uint4*>(op.frag);
@@ -29,6 +31,7 @@ struct BMrhsPolicy {
   }
   __device__ int adjoint() const { return 0; }
   __device__ void finish(const MrhsGroup& gr, int x, int rt, const MrhsAcc<kMrhsMaxT>& acc) const {
+    const BMApply& a = *pa;
     const BMOp& op = a.ops[gr.tag];
     const int lane = threadIdx.x & 31, t = lane & 3, g = lane >> 2;
     const int r0 = 16 * rt + g;
@@ -74,8 +77,8 @@ struct BMrhsPolicy {
 };
 
 template <int N, int P>
-__global__ void __launch_bounds__((P * (N / 16) + 1) * 32) kb_apply_mrhs(BMApply a, int S, uint32_t SB) {
-  const BMrhsPolicy<N> pol{a, *a.step};
+__global__ void __launch_bounds__(mrhs_threads(N, P), mrhs_min_blocks(N, P)) kb_apply_mrhs(const __grid_constant__ BMApply a, int S, uint32_t SB) {
+  const BMrhsPolicy<N> pol{&a, *a.step};
   mrhs_ring<N, P, kMrhsMaxT>(pol, S, SB, a.err);
 }
 

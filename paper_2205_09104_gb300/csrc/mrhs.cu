@@ -32,27 +32,29 @@ __global__ void k_pack_mrhs(const uint32_t* __restrict__ src, uint32_t* __restri
   }
 }
 
-// complex64 columns x + q*ldx (q < R) -> fragment-native BF16 B operands (layout in mrhs_core.cuh),
-// zeros for the columns R .. 4T-1 of the last tile.
+// complex64 columns x + q*ldx (q < R) -> fragment-native BF16 B operands (layout in
+// mrhs_core.cuh), zeros for the columns R .. 4T-1 of the last tile.  One thread per site, padded
+// column q and entry pair kp (coalesced 16-byte reads along kp); entry pair kp = 8kt + 4w + t
+// feeds word w of lane (2(q%4) + part, t) of tile (q/4, kt), the real part to the even lane.
 __global__ void k_pack_mrhs_x(const float2* __restrict__ x, long long ldx, int R, int T, int V, int n,
                               uint32_t* __restrict__ xb) {
-  const int NT = n / 16;
-  const size_t total = (size_t)V * T * NT * 64;
+  const int NT = n / 16, HP = n / 2;  // entry pairs per vector
+  const size_t total = (size_t)V * (kMrhsTile * T) * HP;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int w = (int)(i & 1), lane = (int)((i >> 1) & 31);
-    size_t rest = i >> 6;
-    const int kt = (int)(rest % NT);
-    rest /= NT;
-    const int tl = (int)(rest % T);
-    const size_t site = rest / T;
-    const int g = lane >> 2, t = lane & 3;
-    const int q = kMrhsTile * tl + (g >> 1);
-    uint32_t v = 0u;
+    const int kp = (int)(i % HP);
+    const size_t rest = i / HP;
+    const int q = (int)(rest % (kMrhsTile * T));
+    const size_t site = rest / (kMrhsTile * T);
+    uint32_t re = 0u, im = 0u;
     if (q < R) {
-      const float4 e = __ldg(reinterpret_cast<const float4*>(x + q * ldx + site * n + 16 * kt + 2 * t + 8 * w));
-      v = (g & 1) ? bf2_bits(e.y, e.w) : bf2_bits(e.x, e.z);
+      const float4 e = __ldg(reinterpret_cast<const float4*>(x + q * ldx + site * n + 2 * kp));
+      re = bf2_bits(e.x, e.z);
+      im = bf2_bits(e.y, e.w);
     }
-    xb[i] = v;
+    const int kt = kp >> 3, w = (kp >> 2) & 1, t = kp & 3, tl = q / kMrhsTile, g = 2 * (q % kMrhsTile);
+    uint32_t* dst = xb + ((site * T + tl) * NT + kt) * 64 + (4 * g + t) * 2 + w;
+    dst[0] = re;
+    dst[8] = im;  // lane + 4 (g + 1)
   }
 }
 
@@ -78,12 +80,15 @@ template <int N, int P> struct MrhsShape {
   static constexpr int THREADS = (WC + 1) * 32;
 };
 
-// One operator, columns x + q*ldx, plain or adjoint product.
+// One operator, columns x + q*ldx, plain or adjoint product (a: the kernel's __grid_constant__
+// parameter, read through the constant bank rather than copied into registers).
 template <int N, int T>
 struct MrhsPlain {
-  MrhsArgs a;
-  __device__ int ngroups(int P) const { return (a.V + P - 1) / P; }
+  static constexpr bool kRuntimeT = false;
+  const MrhsArgs* pa;
+  __device__ int ngroups(int P) const { return (pa->V + P - 1) / P; }
   __device__ MrhsGroup group(int g, int P) const {
+    const MrhsArgs& a = *pa;
     MrhsGroup r;
     r.frag = a.frag;
     r.nb = a.nb;
@@ -95,8 +100,9 @@ struct MrhsPlain {
     r.tag = 0;
     return r;
   }
-  __device__ int adjoint() const { return a.adj; }
+  __device__ int adjoint() const { return pa->adj; }
   __device__ void finish(const MrhsGroup&, int x, int rt, const MrhsAcc<T>& acc) const {
+    const MrhsArgs& a = *pa;
     const int lane = threadIdx.x & 31, t = lane & 3, g = lane >> 2;
 #pragma unroll
     for (int tl = 0; tl < T; ++tl) {
@@ -112,8 +118,8 @@ struct MrhsPlain {
 };
 
 template <int N, int T, int P>
-__global__ void __launch_bounds__(MrhsShape<N, P>::THREADS) k_apply_mrhs(MrhsArgs a) {
-  mrhs_ring<N, P, T>(MrhsPlain<N, T>{a}, a.S, a.SB, a.err);
+__global__ void __launch_bounds__(mrhs_threads(N, P), mrhs_min_blocks(N, P)) k_apply_mrhs(const __grid_constant__ MrhsArgs a) {
+  mrhs_ring<N, P, T>(MrhsPlain<N, T>{&a}, a.S, a.SB, a.err);
 }
 
 constexpr int kMrhsMaxSmem = 200 * 1024;
@@ -238,7 +244,7 @@ int launch_apply_mrhs_bf16(const coarse_op* op, const void* x, void* y, int nrhs
     a.R = nrhs - c0 < kMrhsPass ? nrhs - c0 : kMrhsPass;
     {
       const int T = (a.R + kMrhsTile - 1) / kMrhsTile;
-      const size_t total = (size_t)op->V * T * (op->n / 16) * 64;
+      const size_t total = (size_t)op->V * (kMrhsTile * T) * (op->n / 2);
       size_t grid = (total + 255) / 256;
       if (grid > (size_t)sm_count() * 16) grid = (size_t)sm_count() * 16;
       k_pack_mrhs_x<<<(int)grid, 256, 0, s>>>(a.x, a.ldx, a.R, T, op->V, op->n, (uint32_t*)op->mrhs_x.ptr);

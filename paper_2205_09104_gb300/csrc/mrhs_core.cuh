@@ -76,10 +76,11 @@ __device__ __forceinline__ uint32_t s3mask(int k0, int nv) { return k0 < nv ? 0u
 // One staged block (all NT x NT tiles, fragment layout) times the staged vectors of its source site.
 // Forward / self blocks (bwd = 0): P += F w with w = (adj ? s3 x : x), rows of tile rt.
 // Backward blocks (bwd = 1): Q += F^T-products on (adj ? x : s3 x), columns of tile rt (F^H w).
-// Tiles tl >= Tn (the site's own tile count, <= T) are skipped.
-template <int N, int T>
+// Column tiles 0 .. T-1 of accumulators sized TA >= T (T is a compile-time count so that the
+// unrolled loops carry no branches).
+template <int N, int T, int TA = T>
 __device__ __forceinline__ void mrhs_block(const uint4* blk, const uint2* vec, int rt, int bwd, int adj,
-                                           MrhsAcc<T>& acc, int Tn = T) {
+                                           MrhsAcc<TA>& acc) {
   constexpr int NT = N / 16;
   const int lane = threadIdx.x & 31;
   const int flip = bwd ? !adj : adj;  // sigma3 on the B operand
@@ -96,7 +97,6 @@ __device__ __forceinline__ void mrhs_block(const uint4* blk, const uint2* vec, i
     const uint32_t nl = flip ? s3mask(16 * kt, N / 2) : 0u, nh = flip ? s3mask(16 * kt + 8, N / 2) : 0u;
 #pragma unroll
     for (int tl = 0; tl < T; ++tl) {
-      if (tl >= Tn) break;
       const uint2 bv = vec[(tl * NT + kt) * 32 + lane];
       const uint32_t b0 = bv.x ^ nl, b1 = bv.y ^ nh;
       if (!bwd) {

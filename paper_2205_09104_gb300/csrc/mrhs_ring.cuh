@@ -2,6 +2,7 @@
 // come from and what happens to the results (a policy class):
 //
 //   struct Policy {
+//     static constexpr bool kRuntimeT;                      // operators with fewer tiles than TACC
 //     __device__ int ngroups(int P) const;                  // site groups of P sites
 //     __device__ MrhsGroup group(int g, int P) const;       // blocks / vectors / sites of group g
 //     __device__ int adjoint() const;
@@ -33,6 +34,13 @@ struct MrhsGroup {
   int tag;            // policy data (e.g. the operator index)
 };
 
+// Threads of a CTA (consumer warps + the producer warp) and the CTAs per SM to reserve registers
+// for (at most 128 registers per thread).
+__host__ __device__ constexpr int mrhs_threads(int N, int P) { return (P * (N / 16) + 1) * 32; }
+__host__ __device__ constexpr int mrhs_min_blocks(int N, int P) {
+  return 65536 / (mrhs_threads(N, P) * 128) > 0 ? 65536 / (mrhs_threads(N, P) * 128) : 1;
+}
+
 __host__ __device__ constexpr uint32_t mrhs_stage_bytes(int N, int P, int TACC) {
   return (uint32_t)P * (4u * N * N + (uint32_t)TACC * (N / 16) * 256u);
 }
@@ -62,25 +70,36 @@ __device__ __forceinline__ void mrhs_ring(const Policy& pol, int S, uint32_t SB,
     // keep the site's neighbour row in registers for the group's 9 items.
     const int p = lane < P ? lane : lane - P;
     const bool active = lane < 2 * P;
-    MrhsGroup gr{};
-    int4 nb_lo = make_int4(0, 0, 0, 0), nb_hi = nb_lo;
+    // the next group's description and neighbour rows are fetched one group ahead, so that
+    // their latency never stalls the copies
+    auto fetch = [&](int k, MrhsGroup& g, int4& lo, int4& hi) {
+      const int gi = (int)blockIdx.x + k * (int)gridDim.x;
+      if (gi >= ngroups) return;
+      g = pol.group(gi, P);
+      if (active && p < g.np) {
+        const int x = g.x0 + p;
+        lo = __ldg(reinterpret_cast<const int4*>(g.nb + x * 8));
+        hi = __ldg(reinterpret_cast<const int4*>(g.nb + x * 8 + 4));
+      }
+    };
+    MrhsGroup gr{}, gn{};
+    int4 nb_lo = make_int4(0, 0, 0, 0), nb_hi = nb_lo, nx_lo = nb_lo, nx_hi = nb_lo;
+    fetch(0, gn, nx_lo, nx_hi);
     int ok = 1;
     int it = 0;
     for (; it < items; ++it) {
       const int slot = it % S;
       const int b = it % 9;
       if (b == 0) {
-        gr = pol.group((int)blockIdx.x + (it / 9) * (int)gridDim.x, P);
-        if (active && p < gr.np) {
-          const int x = gr.x0 + p;
-          nb_lo = __ldg(reinterpret_cast<const int4*>(gr.nb + x * 8));
-          nb_hi = __ldg(reinterpret_cast<const int4*>(gr.nb + x * 8 + 4));
-        }
+        gr = gn;
+        nb_lo = nx_lo;
+        nb_hi = nx_hi;
+        fetch(it / 9 + 1, gn, nx_lo, nx_hi);
       }
       if (it >= S && lane == 0) ok = mbar_wait_suspend(empty + slot, (uint32_t)((it / S - 1) & 1)) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
-      const uint32_t VB = (uint32_t)gr.T * NT * 256u;
+      const uint32_t VB = (uint32_t)(Policy::kRuntimeT ? gr.T : TACC) * NT * 256u;
       unsigned char* st = smem + (size_t)slot * SB;
       if (lane == 0) mbar_expect_tx(full + slot, (uint32_t)gr.np * (BLK + VB));
       __syncwarp();
@@ -127,11 +146,20 @@ __device__ __forceinline__ void mrhs_ring(const Policy& pol, int S, uint32_t SB,
     if (!mbar_wait_suspend(full + slot, (uint32_t)((it / S) & 1))) ok = 0;
     if (!__all_sync(0xffffffffu, ok)) break;
     const bool valid = p < gr.np;
-    const uint32_t VB = (uint32_t)gr.T * NT * 256u;
+    const int Tn = Policy::kRuntimeT ? gr.T : TACC;  // compile-time for single-shape policies
+    const uint32_t VB = (uint32_t)Tn * NT * 256u;
     const unsigned char* st = smem + (size_t)slot * SB;
-    if (valid)
-      mrhs_block<N, TACC>(reinterpret_cast<const uint4*>(st + p * BLK),
-                          reinterpret_cast<const uint2*>(st + P * BLK + p * VB), rt, b >= 5, adj, acc, gr.T);
+    if (valid) {
+      const uint4* blk = reinterpret_cast<const uint4*>(st + p * BLK);
+      const uint2* vec = reinterpret_cast<const uint2*>(st + P * BLK + p * VB);
+      if constexpr (Policy::kRuntimeT) {  // warp-uniform dispatch on the operator's tile count
+        if (Tn == 1) mrhs_block<N, 1, TACC>(blk, vec, rt, b >= 5, adj, acc);
+        else if (TACC >= 2 && Tn == 2) mrhs_block<N, (TACC >= 2 ? 2 : 1), TACC>(blk, vec, rt, b >= 5, adj, acc);
+        else mrhs_block<N, TACC, TACC>(blk, vec, rt, b >= 5, adj, acc);
+      } else {
+        mrhs_block<N, TACC, TACC>(blk, vec, rt, b >= 5, adj, acc);
+      }
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty + slot);
     if (b == 8) {
