@@ -123,9 +123,12 @@ def run_gb300(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     prec = cg.PREC_BF16 if args.prec == "bf16" else cg.PREC_FP32
+    poly_bf16 = prec == cg.PREC_FP32 and args.poly == "bf16"
+    extra = cg.COARSE_POLY_BF16 if poly_bf16 else 0
     # replicas: each rank solves its own right-hand sides with its own copy of the operator
     op = build_coarse_operator(KEY, FINE_DIMS, NV, M0, CSW, device=dev)
-    cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(prec,))
+    cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv,
+                      precisions=(prec, cg.PREC_BF16) if poly_bf16 else (prec,))
     host_blocks = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         host_blocks = (op.self_blocks.cpu().numpy(), op.hop_blocks.cpu().numpy(), op.dims)
@@ -138,9 +141,9 @@ def run_gb300(args):
     S = torch.from_numpy(draws.rhs((*KEY, 50 + rank), 4, N)).to(dev)  # setup right-hand sides
     X = torch.zeros_like(B)
     inner_tol = 1e-5 if prec == cg.PREC_FP32 else 1e-2
-    p = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS, **PARAMS)
-    pt = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS | cg.COARSE_TIME_APPLY,
-                         **PARAMS)
+    p = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS | extra, **PARAMS)
+    pt = cg.solve_params(precision=prec, inner_tol=inner_tol,
+                         flags=cg.COARSE_ZERO_GUESS | cg.COARSE_TIME_APPLY | extra, **PARAMS)
     # setup: the polynomial and the first u recycle-space updates (after u updates U_k, C_k
     # stay frozen for all later solves with this operator, Sec. 4.1.1); reported separately
     t_setup = time.perf_counter()
@@ -200,13 +203,14 @@ def run_gb300(args):
         t = torch.tensor([ms_e2e], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_e2e = float(t.item())
-    # roofline of the stencil apply (the dominant kernel): algorithmic bytes per launch
-    esize = 4 if prec == cg.PREC_BF16 else 8
-    bytes_per_apply = 5 * n * n * V * esize + 2 * N * 8
+    # roofline of the stencil apply (the dominant kernel): algorithmic bytes of every timed launch
+    # (5 n^2 V block bytes of its precision + 2 N vector bytes) over their summed device time
     apply_ms = sum(i["apply_ms"] for i in infos)
     apply_cnt = sum(i["apply_count"] for i in infos)
+    apply_bytes = sum(i["apply_bytes"] for i in infos)
     avg = apply_ms / max(apply_cnt, 1)
-    achieved = bytes_per_apply / (avg * 1e-3) / 1e9
+    bytes_per_apply = apply_bytes / max(apply_cnt, 1)
+    achieved = apply_bytes / (apply_ms * 1e-3) / 1e9
     peak, src = peaks()
     iters = statistics.mean(i["iterations"] for i in infos)
     line = {
@@ -224,14 +228,16 @@ def run_gb300(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD.format(prec=args.prec.upper()), "l2": "inputs larger than L2 "
                    "(FP64 blocks 335 MB read every refinement step; FP32 blocks 168 MB)",
+                   "polynomial_chain_blocks": "bf16" if poly_bf16 else args.prec,
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(world * args.steps / (ms_e2e / 1e3), 3), "unit": "solves/s",
                 "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
         "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": f"k_apply<32,{'cbf16' if esize == 4 else 'float2'}>",
-                     "bytes_per_launch": bytes_per_apply, "avg_launch_us": round(avg * 1e3, 2),
+                     "kernel": ("k_apply_tma<32,float2> (operator) + k_apply_tma<32,cbf16> (polynomial chain)"
+                                if poly_bf16 else f"k_apply_tma<32,{'cbf16' if prec == cg.PREC_BF16 else 'float2'}>"),
+                     "bytes_per_launch": round(bytes_per_apply), "avg_launch_us": round(avg * 1e3, 2),
                      "launches_timed": apply_cnt, "peak_source": src},
         "solver": {"iterations_per_solve": iters, "matvecs_per_solve": statistics.mean(i["matvecs"] for i in infos),
                    "ir_steps": statistics.mean(i["ir_steps"] for i in infos), "worst_rel_residual": worst_res,
@@ -239,6 +245,7 @@ def run_gb300(args):
                    "setup": {"solves": setup_solves, "seconds": round(t_setup, 3),
                              "what": "polynomial + recycle-space updates until u=10 is reached"}},
         "clocks": clk.summary(),
+        "autotune": cg.autotune_report().strip().split("\n"),
     }
     if args.fp64_baseline_steps > 0:
         # plain FP64 GPU GMRES(50) on the same right-hand sides: the reference point of the speedup
@@ -393,7 +400,8 @@ def run_apply_only(args):
                       "l2_flush": not args.no_flush, "median_us": round(med * 1e3, 2), "min_us": round(min(ts) * 1e3, 2),
                       "bytes_per_launch": nbytes, "achieved_gbs": round(nbytes / (med * 1e-3) / 1e9, 1),
                       "peak_gbs": peak, "frac": round(nbytes / (med * 1e-3) / 1e9 / peak, 4), "peak_source": src,
-                      "gflops": round(flops / (med * 1e-3) / 1e9, 1), "launches": len(ts)}), flush=True)
+                      "gflops": round(flops / (med * 1e-3) / 1e9, 1), "launches": len(ts),
+                      "autotune": cg.autotune_report().strip().split("\n")}), flush=True)
     cop.close()
 
 
@@ -519,6 +527,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--poly", default="bf16", choices=["bf16", "same"],
+                    help="blocks of the polynomial-chain applies for FP32 inner solves (COARSE_POLY_BF16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--apply-only", choices=sorted(APPLY_CASES), default=None,

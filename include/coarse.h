@@ -150,6 +150,14 @@ int coarse_residual_noalloc(const coarse_op* op, const void* b, const void* x, v
 #define COARSE_REBUILD_POLY 0x2u    /* recompute the polynomial before this solve */
 #define COARSE_RESET_RECYCLE 0x4u   /* drop the GCRO-DR recycle space before this solve */
 #define COARSE_TIME_APPLY 0x8u      /* time every inner-precision stencil launch with CUDA events */
+/* Evaluate the polynomial preconditioner q (Sec. 3.3) with the operator's BF16 blocks (FP32
+ * vectors and accumulation) while the Krylov operator itself keeps the inner-precision blocks.
+ * q(BF16 blocks) is still one fixed linear operator, so right-preconditioned GMRES and the
+ * GCRO-DR recycle space (built for that operator; rebuilt when the choice changes) stay exact;
+ * only the preconditioner's quality changes, by the 2^-9 block rounding.  Takes effect for
+ * precision COARSE_PREC_FP32 on operators created with BF16 enabled; ignored otherwise and by
+ * coarse_solve_batched.  The paper has no counterpart (its coarsest level is single precision). */
+#define COARSE_POLY_BF16 0x10u
 
 typedef struct {
   int32_t m;               /* restart length of GMRES / GCRO-DR (Sec. 3.1), 2 .. 64 */
@@ -161,7 +169,8 @@ typedef struct {
   int32_t precision;       /* coarse_precision of the inner solver; FP64 = no refinement */
   double inner_tol;        /* relative residual target of each inner solve (FP32/BF16 only) */
   int32_t max_ir;          /* FP64 iterative-refinement steps allowed */
-  uint32_t flags;          /* COARSE_ZERO_GUESS | COARSE_REBUILD_POLY | COARSE_RESET_RECYCLE */
+  uint32_t flags;          /* COARSE_ZERO_GUESS | COARSE_REBUILD_POLY | COARSE_RESET_RECYCLE |
+                              COARSE_TIME_APPLY | COARSE_POLY_BF16 */
   uint64_t seed;           /* seeds the polynomial start vector when poly_start is NULL */
   const void* poly_start;  /* optional device complex128 [V][n]: start vector of the polynomial's Arnoldi */
 } coarse_solve_params;
@@ -179,6 +188,8 @@ typedef struct {
   double apply_ms;         /* device time of the inner-precision stencil launches (COARSE_TIME_APPLY) */
   int32_t apply_count;     /* stencil launches timed in apply_ms */
   int32_t kernel_launches; /* kernels this call launched */
+  double apply_bytes;      /* algorithmic bytes of the stencil launches timed in apply_ms
+                              (5 n^2 V block bytes + 2 N vector bytes each, by their precision) */
 } coarse_solve_info;
 
 /*

@@ -13,6 +13,7 @@ COARSE_ZERO_GUESS = 0x1
 COARSE_REBUILD_POLY = 0x2
 COARSE_RESET_RECYCLE = 0x4
 COARSE_TIME_APPLY = 0x8
+COARSE_POLY_BF16 = 0x10
 
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "BREAKDOWN",
           -6: "NONFINITE", -7: "TIMEOUT", -8: "NOT_GAMMA5"}
@@ -46,7 +47,8 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("matvecs", ctypes.c_int32),
                 ("cycles", ctypes.c_int32), ("ir_steps", ctypes.c_int32), ("recycle_updates", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
-                ("apply_ms", ctypes.c_double), ("apply_count", ctypes.c_int32), ("kernel_launches", ctypes.c_int32)]
+                ("apply_ms", ctypes.c_double), ("apply_count", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("apply_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

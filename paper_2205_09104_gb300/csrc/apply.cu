@@ -14,10 +14,14 @@
 //   forward use  y_i  += F_ij w_j : n/4 row partial sums per lane, reduced over t
 //   transposed   y'_j += conj(F_ij) w'_i : CPL column sums per lane, reduced over g
 // without shared-memory staging of the block.
+#include <algorithm>
+#include <cstdio>
+
 #include "common.cuh"
 #include "apply_core.cuh"
 #include "batch.cuh"
 #include "pipe.cuh"
+#include "tune.cuh"
 
 namespace coarse {
 
@@ -386,12 +390,64 @@ __global__ void __launch_bounds__(128) kb_residual64(BApply b, const double2* co
 
 }  // namespace
 
+// FP32 / BF16: the autotuner picks, per (precision, n, lattice-size bucket), between the
+// TMA-staged persistent kernel (candidate 0, the default) and the register push-pull kernel
+// (candidate 1).  Candidates are timed in plain mode into a scratch output, so that an epilogue
+// that accumulates (the polynomial chain) never runs twice; decisions are cached per process.
+template <class BT>
+int launch_tuned(int prec, int n, const ApplyArgs& a, cudaStream_t s) {
+  static int choice[3][32];  // [n/16 - 1][bucket]: -1 unknown
+  static bool init = false;
+  if (!init) {
+    for (auto& row : choice)
+      for (int& c : row) c = -1;
+    init = true;
+  }
+  const int ni = n / 16 - 1, vb = std::min(tune_bucket(a.V), 31);
+  if (ni < 0 || ni > 2) {
+    set_error("coarse_apply: unsupported n = %d (nv must be 8, 16 or 24)", n);
+    return COARSE_ERR_INVALID_ARG;
+  }
+  if (choice[ni][vb] < 0) {
+    char key[64];
+    snprintf(key, sizeof(key), "apply/p%d/n%d/v%d", prec, n, vb);
+    void* scratch = nullptr;
+    auto run = [&](const TuneChoice& c) -> int {
+      if (!scratch && cudaMalloc(&scratch, sizeof(float2) * (size_t)a.V * n) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("coarse_apply: autotuner scratch allocation failed");
+        return COARSE_ERR_OOM;
+      }
+      ApplyArgs t = a;
+      t.mode = APPLY_PLAIN;
+      t.y = scratch;
+      t.z = nullptr;
+      t.acc = nullptr;
+      t.coef = nullptr;
+      t.stop = nullptr;
+      return c.a == 1 ? launch_t<BT, float2, float2>(n, t, s) : launch_tma<BT>(n, t, s);
+    };
+    TuneChoice c;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    const int rc = tune_pick(key, {TuneChoice{0, 0, 0}, TuneChoice{1, 0, 0}}, run, s, &c);
+    if (scratch) {
+      cudaStreamSynchronize(s);
+      cudaFree(scratch);
+    }
+    if (rc != COARSE_OK) return rc;
+    if (cap != cudaStreamCaptureStatusNone) return c.a == 1 ? launch_t<BT, float2, float2>(n, a, s) : launch_tma<BT>(n, a, s);
+    choice[ni][vb] = c.a;
+  }
+  return choice[ni][vb] == 1 ? launch_t<BT, float2, float2>(n, a, s) : launch_tma<BT>(n, a, s);
+}
+
 int launch_apply(int prec, int n, const ApplyArgs& a, cudaStream_t s) {
   if (a.V <= 0) return COARSE_OK;
   switch (prec) {
     case COARSE_PREC_FP64: return launch_t<double2, double2, double2>(n, a, s);
-    case COARSE_PREC_FP32: return launch_tma<float2>(n, a, s);
-    case COARSE_PREC_BF16: return launch_tma<cbf16>(n, a, s);
+    case COARSE_PREC_FP32: return launch_tuned<float2>(prec, n, a, s);
+    case COARSE_PREC_BF16: return launch_tuned<cbf16>(prec, n, a, s);
   }
   set_error("coarse_apply: unknown precision %d", prec);
   return COARSE_ERR_INVALID_ARG;

@@ -144,26 +144,29 @@ int Solver::ensure(int m, int k, int dmax) {
   return COARSE_OK;
 }
 
-int Solver::apply(const void* x, void* y, int mode, void* accp, const double2* coef, const int* stop) {
-  ApplyArgs a = make_apply_args(op, prec, x, y);
+int Solver::apply(const void* x, void* y, int mode, void* accp, const double2* coef, const int* stop, int bprec) {
+  if (bprec < 0) bprec = prec;
+  ApplyArgs a = make_apply_args(op, bprec, x, y);
   a.acc = accp;
   a.coef = coef;
   a.mu = mu_eff;
   a.mode = mode;
   a.stop = stop;
   ++matvecs;
-  if (!time_apply) return launch_apply(prec, op->n, a, stream);
+  if (!time_apply) return launch_apply(bprec, op->n, a, stream);
   while (ev_pool.size() < 2) {
     cudaEvent_t ev;
     COARSE_CUDA(cudaEventCreate(&ev));
     ev_pool.push_back(ev);
   }
-  Timed tm{cur_tag, ev_pool.back(), nullptr};
+  const double esz[3] = {16.0, 8.0, 4.0}, vsz = v64 ? 16.0 : 8.0;
+  Timed tm{cur_tag, ev_pool.back(), nullptr,
+           5.0 * op->n * op->n * (double)op->V * esz[bprec] + 2.0 * (double)N * vsz};
   ev_pool.pop_back();
   tm.b = ev_pool.back();
   ev_pool.pop_back();
   COARSE_CUDA(cudaEventRecord(tm.a, stream));
-  TRY(launch_apply(prec, op->n, a, stream));
+  TRY(launch_apply(bprec, op->n, a, stream));
   COARSE_CUDA(cudaEventRecord(tm.b, stream));
   timed.push_back(tm);
   return COARSE_OK;
@@ -175,6 +178,7 @@ void Solver::harvest(int steps_done) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, tm.a, tm.b) == cudaSuccess) {
         apply_ms += ms;
+        apply_bytes += tm.bytes;
         ++apply_count;
       }
     }
@@ -192,11 +196,11 @@ int Solver::precondition(const void* v, const void** res, const int* stop) {
     *res = acc;
     return COARSE_OK;
   }
-  TRY(apply(v, sa, APPLY_POLY_FIRST, acc, dn.polyc, stop));
+  TRY(apply(v, sa, APPLY_POLY_FIRST, acc, dn.polyc, stop, poly_prec));
   void* cur = sa;
   void* nxt = sb;
   for (int i = 2; i < d; ++i) {
-    TRY(apply(cur, nxt, APPLY_POLY, acc, dn.polyc + 3 * (i - 1), stop));
+    TRY(apply(cur, nxt, APPLY_POLY, acc, dn.polyc + 3 * (i - 1), stop, poly_prec));
     void* tt = cur; cur = nxt; nxt = tt;
   }
   *res = acc;
@@ -439,14 +443,20 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
   const int k = p->defl_k;
   const int dd = p->poly_degree;
   TRY(s->ensure(m, k, dd > 0 ? dd : 1));
-  if (p->flags & COARSE_RESET_RECYCLE) {
+  s->poly_prec = ((p->flags & COARSE_POLY_BF16) && s->prec == COARSE_PREC_FP32 && op->blk[COARSE_PREC_BF16].ptr)
+                     ? COARSE_PREC_BF16
+                     : s->prec;
+  if ((p->flags & COARSE_RESET_RECYCLE) || s->rec_poly_prec != s->poly_prec) {
+    // the recycle space spans C = A q(A) U for one fixed q: drop it when q's blocks change
     s->k_cur = 0;
     s->updates = 0;
   }
+  s->rec_poly_prec = s->poly_prec;
   const long long mv0 = s->matvecs;
   const long long launches0 = launches_so_far();
   s->time_apply = (p->flags & COARSE_TIME_APPLY) != 0;
   s->apply_ms = 0.0;
+  s->apply_bytes = 0.0;
   s->apply_count = 0;
   if (!s->poly_ok || (p->flags & COARSE_REBUILD_POLY) || s->d_cap < dd || (dd > 0 && s->d == 0) ||
       (dd == 0 && s->d != 0)) {
@@ -491,6 +501,7 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
   s->harvest(1 << 30);
   s->time_apply = false;
   inf.apply_ms = s->apply_ms;
+  inf.apply_bytes = s->apply_bytes;
   inf.apply_count = (int)s->apply_count;
   inf.kernel_launches = (int)(launches_so_far() - launches0);
   inf.matvecs = (int)(s->matvecs - mv0);

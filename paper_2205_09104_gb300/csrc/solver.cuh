@@ -60,17 +60,22 @@ struct Solver {
   // optional CUDA-event timing of the stencil launches (COARSE_TIME_APPLY)
   bool time_apply = false;
   int cur_tag = -1;                 // Arnoldi step of the applies being launched (-1: not gated)
-  struct Timed { int tag; cudaEvent_t a, b; };
+  struct Timed { int tag; cudaEvent_t a, b; double bytes; };
   std::vector<Timed> timed;         // launched, not yet harvested
   std::vector<cudaEvent_t> ev_pool;
   double apply_ms = 0.0;
+  double apply_bytes = 0.0;         // algorithmic bytes of the timed launches
   long long apply_count = 0;
+  // blocks of the polynomial-chain applies (COARSE_POLY_BF16: BF16 while the Krylov operator keeps
+  // `prec`); the recycle space belongs to the preconditioned operator of `rec_poly_prec`
+  int poly_prec = COARSE_PREC_FP32;
+  int rec_poly_prec = -1;
   void harvest(int steps_done);     // after a stream sync: add the elapsed time of the applies that ran
 
   ~Solver();
   void release();
   int ensure(int m, int k, int dmax);
-  int apply(const void* x, void* y, int mode, void* accp, const double2* coef, const int* stop);
+  int apply(const void* x, void* y, int mode, void* accp, const double2* coef, const int* stop, int bprec = -1);
   int precondition(const void* v, const void** res, const int* stop);
   int opA(const void* v, void* out, const int* stop);
   int read_state();
