@@ -418,8 +418,14 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
     return launch_norm2(1, r64, N, op->norms, op->red, op->counter, stream);
   };
 
-  if (p->flags & COARSE_ZERO_GUESS) COARSE_CUDA(cudaMemsetAsync(x64, 0, sizeof(double2) * (size_t)N, stream));
-  TRY(residual());
+  if (p->flags & COARSE_ZERO_GUESS) {
+    // x = 0: r = b exactly, no stencil launch needed
+    COARSE_CUDA(cudaMemsetAsync(x64, 0, sizeof(double2) * (size_t)N, stream));
+    COARSE_CUDA(cudaMemcpyAsync(r64, b64, sizeof(double2) * (size_t)N, cudaMemcpyDeviceToDevice, stream));
+    TRY(launch_norm2(1, r64, N, op->norms, op->red, op->counter, stream));
+  } else {
+    TRY(residual());
+  }
   TRY(launch_norm2(1, b64, N, op->norms + 1, op->red, op->counter, stream));
   COARSE_CUDA(cudaMemcpyAsync(hn, op->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
   COARSE_CUDA(cudaStreamSynchronize(stream));
