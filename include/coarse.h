@@ -116,6 +116,18 @@ int coarse_apply(const coarse_op* op, const void* x, void* y, int nrhs, int prec
 int coarse_apply_adjoint(const coarse_op* op, const void* x, void* y, int nrhs, int precision, void* stream);
 
 /*
+ * coarse_schur_apply -- y = S x with S = 1 - D_ee^{-1} D_eo D_oo^{-1} D_oe, the odd-even
+ * reduced coarse operator with block-Jacobi left preconditioning (Sec. 2, Sec. 3.2),
+ * applied in factored form (two passes over the lattice, each hop block read once
+ * per pass, the diagonal-block inverses applied explicitly).
+ * x, y : device [V/2][n] on the even sites in increasing site order (site parity =
+ *        (x0 + x1 + x2 + x3) mod 2), complex128 for FP64, complex64 otherwise; no overlap.
+ * Needs even lattice extents.  Asynchronous, except that the first call (and the
+ * first after coarse_op_update) computes the inverses and synchronises `stream`.
+ */
+int coarse_schur_apply(coarse_op* op, const void* x, void* y, int precision, void* stream);
+
+/*
  * coarse_residual -- r = b - D_c x in FP64 and the norms ||r||_2, ||b||_2.
  * b, x, r : device complex128 [V][n] (one right-hand side); r may alias neither.
  * norms_host : host double[2] receiving (||r||, ||b||); the call synchronises `stream`.
@@ -158,6 +170,15 @@ int coarse_residual_noalloc(const coarse_op* op, const void* b, const void* x, v
  * precision COARSE_PREC_FP32 on operators created with BF16 enabled; ignored otherwise and by
  * coarse_solve_batched.  The paper has no counterpart (its coarsest level is single precision). */
 #define COARSE_POLY_BF16 0x10u
+/* Solve through the odd-even reduced system with block-Jacobi left preconditioning
+ * (Sec. 2 and Sec. 3.2): the inner solver (GMRES / polynomial / GCRO-DR) works on
+ * S = 1 - D_ee^{-1} D_eo D_oo^{-1} D_oe over the even sites, with right-hand side
+ * D_ee^{-1} (r_e - D_eo D_oo^{-1} r_o), and the odd sites are retrieved as
+ * D_oo^{-1} (r_o - D_oe e_e); the FP64 refinement around it keeps the full operator.
+ * Needs even lattice extents and precision FP32 or BF16 (COARSE_ERR_INVALID_ARG
+ * otherwise); not for coarse_solve_adjoint; ignored by coarse_solve_batched.  The
+ * first use computes the inverses of the diagonal blocks A_x + i mu sigma3 in FP64. */
+#define COARSE_ODD_EVEN 0x20u
 
 typedef struct {
   int32_t m;               /* restart length of GMRES / GCRO-DR (Sec. 3.1), 2 .. 64 */

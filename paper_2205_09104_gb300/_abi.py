@@ -14,6 +14,7 @@ COARSE_REBUILD_POLY = 0x2
 COARSE_RESET_RECYCLE = 0x4
 COARSE_TIME_APPLY = 0x8
 COARSE_POLY_BF16 = 0x10
+COARSE_ODD_EVEN = 0x20
 
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "BREAKDOWN",
           -6: "NONFINITE", -7: "TIMEOUT", -8: "NOT_GAMMA5"}
@@ -22,7 +23,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED"
 EXPORTS = ["coarse_op_create", "coarse_op_update", "coarse_op_destroy", "coarse_apply", "coarse_apply_adjoint",
            "coarse_residual", "coarse_solve", "coarse_solve_adjoint", "coarse_solve_batched", "coarse_block_grad",
            "coarse_op_poly", "coarse_last_error", "coarse_version", "coarse_residual_noalloc",
-           "coarse_autotune_report"]
+           "coarse_autotune_report", "coarse_schur_apply"]
 
 
 class CoarseError(RuntimeError):
@@ -75,6 +76,7 @@ def lib() -> ctypes.CDLL:
     L.coarse_apply.argtypes = [vp, vp, vp, i32, i32, vp]
     L.coarse_apply_adjoint.argtypes = [vp, vp, vp, i32, i32, vp]
     L.coarse_residual.argtypes = [vp, vp, vp, vp, P(dbl), vp]
+    L.coarse_schur_apply.argtypes = [vp, vp, vp, i32, vp]
     L.coarse_residual_noalloc.argtypes = [vp, vp, vp, vp, P(dbl), vp]
     L.coarse_solve.argtypes = [vp, vp, vp, i32, P(SolveParams), P(SolveInfo), vp]
     L.coarse_solve_adjoint.argtypes = [vp, vp, vp, i32, P(SolveParams), P(SolveInfo), vp]

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "oddeven.cuh"
 #include "solver.cuh"
 
 namespace coarse {
@@ -64,6 +65,13 @@ void free_op(coarse_op* op) {
     if (op->blk[p].ptr) cudaFree(op->blk[p].ptr);
   }
   if (op->mrhs.ptr) cudaFree(op->mrhs.ptr);
+  for (int p = 0; p < 3; ++p) {
+    delete op->eo_solver[p];
+    if (op->inv[p].ptr) cudaFree(op->inv[p].ptr);
+  }
+  if (op->eo_sites) cudaFree(op->eo_sites);
+  if (op->eo_half) cudaFree(op->eo_half);
+  if (op->eo_scratch) cudaFree(op->eo_scratch);
   if (op->mrhs_x.ptr) cudaFree(op->mrhs_x.ptr);
   if (op->nb) cudaFree(op->nb);
   if (op->work64) cudaFree(op->work64);
@@ -180,9 +188,14 @@ namespace {
 int solve_impl(coarse_op* op, const void* b, void* x, int nrhs, const coarse_solve_params* p,
                coarse_solve_info* info, void* stream, int adjoint) {
   TRY(validate_solve(op, b, x, nrhs, p));
+  const int eo = (p->flags & COARSE_ODD_EVEN) ? 1 : 0;
+  if (eo && (adjoint || p->precision == COARSE_PREC_FP64 || !op->eo_sites)) {
+    set_error("COARSE_ODD_EVEN needs even lattice extents, FP32 or BF16 inner solves and a forward solve");
+    return COARSE_ERR_INVALID_ARG;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   COARSE_CUDA(cudaSetDevice(op->device));
-  Solver* sv = get_solver(op, p->precision, adjoint, s);
+  Solver* sv = get_solver(op, p->precision, adjoint, s, eo);
   const size_t N = (size_t)op->V * op->n;
   int worst = COARSE_OK;
   for (int c = 0; c < nrhs; ++c) {
@@ -278,6 +291,23 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
     if (rc != COARSE_OK) { free_op(op); return rc; } \
   } while (0)
   CREATE_TRY(dmalloc(&op->nb, nb.size() * sizeof(int)));
+  // odd-even site lists (every extent even: each hop joins opposite parities)
+  std::vector<int> eo_sites, eo_half;
+  if (L[0] % 2 == 0 && L[1] % 2 == 0 && L[2] % 2 == 0 && L[3] % 2 == 0) {
+    eo_sites.resize(op->V);
+    eo_half.resize(op->V);
+    int ne = 0, no = op->V / 2;
+    for (int x = 0; x < op->V; ++x) {
+      int c[4], r = x;
+      for (int mu = 0; mu < 4; ++mu) { c[mu] = r % L[mu]; r /= L[mu]; }
+      const bool odd = (c[0] + c[1] + c[2] + c[3]) & 1;
+      const int q = odd ? no++ : ne++;
+      eo_sites[q] = x;
+      eo_half[x] = odd ? q - op->V / 2 : q;
+    }
+    CREATE_TRY(dmalloc(&op->eo_sites, eo_sites.size() * sizeof(int)));
+    CREATE_TRY(dmalloc(&op->eo_half, eo_half.size() * sizeof(int)));
+  }
   for (int p = 0; p < 3; ++p) {
     if (!(op->precisions & (1u << p))) continue;
     op->blk[p].bytes = nblk * esz[p];
@@ -297,7 +327,12 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
   op->coef = (double2*)(op->norms + 8);
   op->counter = (unsigned*)(op->coef + 2);
   const double2 cst[2] = {make_double2(-1.0, 0.0), make_double2(1.0, 0.0)};
-  if (cudaMemcpyAsync(op->nb, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+  if ((op->eo_sites &&
+       (cudaMemcpyAsync(op->eo_sites, eo_sites.data(), eo_sites.size() * sizeof(int), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(op->eo_half, eo_half.data(), eo_half.size() * sizeof(int), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)) ||
+      cudaMemcpyAsync(op->nb, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(op->red, 0, (2 * 304 + 64) * sizeof(double) + 64, s) != cudaSuccess ||
       cudaMemsetAsync(op->apply_cnt, 0, ((size_t)op->V + 4) * sizeof(int), s) != cudaSuccess ||
       cudaMemcpyAsync(op->coef, cst, sizeof(cst), cudaMemcpyHostToDevice, s) != cudaSuccess) {
@@ -316,9 +351,11 @@ int coarse_op_update(coarse_op* op, const void* self_blocks, const void* hop_blo
   TRY(check_ptr(self_blocks, "self_blocks"));
   TRY(check_ptr(hop_blocks, "hop_blocks"));
   TRY(ingest(op, self_blocks, hop_blocks, 0, (cudaStream_t)stream));
+  op->inv_ok = 0;
   for (int p = 0; p < 3; ++p) {
     if (op->solver[p]) op->solver[p]->invalidate();
     if (op->adj_solver[p]) op->adj_solver[p]->invalidate();
+    if (op->eo_solver[p]) op->eo_solver[p]->invalidate();
   }
   return COARSE_OK;
 }
@@ -331,6 +368,22 @@ int coarse_apply(const coarse_op* op, const void* x, void* y, int nrhs, int prec
 
 int coarse_apply_adjoint(const coarse_op* op, const void* x, void* y, int nrhs, int precision, void* stream) {
   return apply_impl(op, x, y, nrhs, precision, stream, 1);
+}
+
+int coarse_schur_apply(coarse_op* op, const void* x, void* y, int precision, void* stream) {
+  if (!op) { set_error("op is NULL"); return COARSE_ERR_INVALID_ARG; }
+  TRY(check_ptr(x, "x"));
+  TRY(check_ptr(y, "y"));
+  if (precision < 0 || precision > 2 || !op->blk[precision].ptr) {
+    set_error("precision %d not available on this operator", precision);
+    return COARSE_ERR_INVALID_ARG;
+  }
+  if (x == y) { set_error("x and y must not overlap"); return COARSE_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(eo_prepare(op, op->mu, s));
+  // odd-site intermediate: the third FP64 work vector (large enough for V/2 * n complex128)
+  void* t = op->work64 + 2 * (size_t)op->V * op->n;
+  return launch_eo_schur(op, precision, op->mu, x, y, t, APPLY_PLAIN, nullptr, nullptr, nullptr, s);
 }
 
 int coarse_residual(const coarse_op* op, const void* b, const void* x, void* r, double* norms_host, void* stream) {

@@ -1,0 +1,37 @@
+// Odd-even reduced system with block-Jacobi left preconditioning (Sec. 2, Sec. 3.2): arguments
+// of the fused half apply and the launchers (oddeven.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace coarse {
+
+struct EoArgs {
+  const void* blocks;   // [V][5][n][n] of the block type
+  const void* inv;      // [V][n][n] inverses of the diagonal blocks A_x + i mu sigma3, same type
+  const int* nb;        // [V][8]
+  const int* sites;     // [V]: the even sites in increasing order, then the odd sites
+  const int* half;      // [V]: position of each site in its parity's list
+  int V;
+  int out_par;          // parity of the output sites (0 even, 1 odd)
+  const void* v;        // hop input, compressed on the other parity (nullptr: no hops)
+  const void* z;        // optional: the inverse acts on z - h instead of h
+  const void* base;     // optional: y = base - u instead of y = u
+  void* y;              // output, compressed on out_par
+  int mode;             // ApplyMode epilogue on y (chain input x = base)
+  void* acc;
+  const double2* coef;
+  const int* stop;      // optional device flag: return if set
+};
+
+// Inverses of the diagonal blocks for the twisted mass mu_eff, in every enabled precision
+// (synchronises s the first time and whenever mu_eff changes sign).
+int eo_prepare(coarse_op* op, double mu_eff, cudaStream_t s);
+int launch_eo_half(int prec, int n, const EoArgs& a, cudaStream_t s);
+int launch_eo_split(int v64, const void* full, const int* sites, int V, int n, void* ev, void* od, cudaStream_t s);
+int launch_eo_merge(int v64, const void* ev, const void* od, const int* sites, int V, int n, void* full, cudaStream_t s);
+// y = S x (compressed even vectors; t: odd scratch), with the polynomial-chain epilogue
+int launch_eo_schur(const coarse_op* op, int prec, double mu_eff, const void* x, void* y, void* t, int mode, void* acc,
+                    const double2* coef, const int* stop, cudaStream_t s);
+
+}  // namespace coarse

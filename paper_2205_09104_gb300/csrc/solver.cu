@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "oddeven.cuh"
 #include "solver.cuh"
 #include "solver_state.cuh"
 
@@ -71,7 +72,7 @@ int Solver::ensure(int m, int k, int dmax) {
   k_cap = k;
   d_cap = dmax;
   const size_t cs = csize(v64);
-  const size_t nvec = (size_t)(m + 1) + 4 * (size_t)k + 8;
+  const size_t nvec = (size_t)(m + 1) + 4 * (size_t)k + 9;
   const size_t vbytes = cs * (size_t)N;
   TRY(dalloc((char**)&vecmem, nvec * vbytes));
   char* p = (char*)vecmem;
@@ -85,6 +86,7 @@ int Solver::ensure(int m, int k, int dmax) {
     for (int i = 0; i < k; ++i) C[b][i] = take();
   }
   r = take(); e = take(); t = take(); sa = take(); sb = take(); acc = take(); w = take(); tmp = take();
+  eo_t = take();
   // small arrays
   const int ldh = kMaxDense + 1;
   const int maxq = kMaxK + kMaxDense + 2;
@@ -146,27 +148,34 @@ int Solver::ensure(int m, int k, int dmax) {
 
 int Solver::apply(const void* x, void* y, int mode, void* accp, const double2* coef, const int* stop, int bprec) {
   if (bprec < 0) bprec = prec;
-  ApplyArgs a = make_apply_args(op, bprec, x, y);
-  a.acc = accp;
-  a.coef = coef;
-  a.mu = mu_eff;
-  a.mode = mode;
-  a.stop = stop;
+  auto launch = [&]() -> int {
+    if (eo) return launch_eo_schur(op, bprec, mu_eff, x, y, eo_t, mode, accp, coef, stop, stream);
+    ApplyArgs a = make_apply_args(op, bprec, x, y);
+    a.acc = accp;
+    a.coef = coef;
+    a.mu = mu_eff;
+    a.mode = mode;
+    a.stop = stop;
+    return launch_apply(bprec, op->n, a, stream);
+  };
   ++matvecs;
-  if (!time_apply) return launch_apply(bprec, op->n, a, stream);
+  if (!time_apply) return launch();
   while (ev_pool.size() < 2) {
     cudaEvent_t ev;
     COARSE_CUDA(cudaEventCreate(&ev));
     ev_pool.push_back(ev);
   }
+  // algorithmic bytes: full stencil 5 n^2 V blocks + vector in/out; S: two half applies, each
+  // reading 4.5 n^2 V block entries, with vector traffic 2.5 x (V n) (in, out, odd intermediate)
   const double esz[3] = {16.0, 8.0, 4.0}, vsz = v64 ? 16.0 : 8.0;
-  Timed tm{cur_tag, ev_pool.back(), nullptr,
-           5.0 * op->n * op->n * (double)op->V * esz[bprec] + 2.0 * (double)N * vsz};
+  const double nn = (double)op->n * op->n * (double)op->V, vn = (double)op->V * op->n;
+  const double bytes = eo ? 9.0 * nn * esz[bprec] + 2.5 * vn * vsz : 5.0 * nn * esz[bprec] + 2.0 * (double)N * vsz;
+  Timed tm{cur_tag, ev_pool.back(), nullptr, bytes};
   ev_pool.pop_back();
   tm.b = ev_pool.back();
   ev_pool.pop_back();
   COARSE_CUDA(cudaEventRecord(tm.a, stream));
-  TRY(launch_apply(bprec, op->n, a, stream));
+  TRY(launch());
   COARSE_CUDA(cudaEventRecord(tm.b, stream));
   timed.push_back(tm);
   return COARSE_OK;
@@ -381,16 +390,17 @@ double now_ms() {
 }
 }  // namespace
 
-Solver* get_solver(coarse_op* op, int prec, int adjoint_system, cudaStream_t stream) {
+Solver* get_solver(coarse_op* op, int prec, int adjoint_system, cudaStream_t stream, int odd_even) {
   // With mu = 0, D_c(-mu) = D_c: the adjoint system reuses the forward solver (polynomial, recycle space).
   const bool separate = adjoint_system && op->mu != 0.0;
-  Solver*& slot = separate ? op->adj_solver[prec] : op->solver[prec];
+  Solver*& slot = odd_even ? op->eo_solver[prec] : (separate ? op->adj_solver[prec] : op->solver[prec]);
   if (slot == nullptr) {
     slot = new Solver();
     slot->op = op;
     slot->prec = prec;
     slot->v64 = prec == COARSE_PREC_FP64;
-    slot->N = op->V * op->n;
+    slot->eo = odd_even;
+    slot->N = odd_even ? op->V * op->n / 2 : op->V * op->n;
     slot->tmp64 = op->work64 + (size_t)op->V * op->n;
     slot->mu_eff = separate ? -op->mu : op->mu;
   }
@@ -448,6 +458,22 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
   const int m = p->m;
   const int k = p->defl_k;
   const int dd = p->poly_degree;
+  float2* eo_full = nullptr;  // odd-even: full-length FP32 residual / correction, then its halves
+  float2 *eo_re = nullptr, *eo_ro = nullptr, *eo_to = nullptr, *eo_eo = nullptr;
+  if (s->eo) {
+    TRY(eo_prepare(op, mu_eff, stream));
+    if (!op->eo_scratch && cudaMalloc(&op->eo_scratch, sizeof(float2) * 3 * (size_t)N) != cudaSuccess) {
+      cudaGetLastError();
+      op->eo_scratch = nullptr;
+      set_error("odd-even: scratch allocation failed");
+      return COARSE_ERR_OOM;
+    }
+    eo_full = (float2*)op->eo_scratch;
+    eo_re = eo_full + N;
+    eo_ro = eo_re + N / 2;
+    eo_to = eo_ro + N / 2;
+    eo_eo = eo_to + N / 2;
+  }
   TRY(s->ensure(m, k, dd > 0 ? dd : 1));
   s->poly_prec = ((p->flags & COARSE_POLY_BF16) && s->prec == COARSE_PREC_FP32 && op->blk[COARSE_PREC_BF16].ptr)
                      ? COARSE_PREC_BF16
@@ -480,6 +506,38 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
       COARSE_CUDA(cudaMemcpyAsync(s->r, r64, sizeof(double2) * (size_t)N, cudaMemcpyDeviceToDevice, stream));
       TRY(s->inner(0.5 * p->tol * bn, p->max_restarts, m, k, p->recycle_updates, &ii));
       TRY(launch_axpy(1, s->e, x64, make_double2(1.0, 0.0), N, nullptr, stream));
+    } else if (s->eo) {
+      // Sec. 2 / Sec. 3.2: solve S e_e = D_ee^{-1} (r_e - D_eo D_oo^{-1} r_o), then
+      // e_o = D_oo^{-1} (r_o - D_oe e_e) = t_o - D_oo^{-1} D_oe e_e with t_o = D_oo^{-1} r_o
+      TRY(launch_to_low(r64, op->norms, eo_full, N, stream));
+      TRY(launch_eo_split(0, eo_full, op->eo_sites, op->V, op->n, eo_re, eo_ro, stream));
+      EoArgs a{};
+      a.blocks = op->blk[s->prec].ptr;
+      a.inv = op->inv[s->prec].ptr;
+      a.nb = op->nb;
+      a.sites = op->eo_sites;
+      a.half = op->eo_half;
+      a.V = op->V;
+      a.mode = APPLY_PLAIN;
+      a.out_par = 1;  // t_o = D_oo^{-1} r_o
+      a.z = eo_ro;
+      a.y = eo_to;
+      TRY(launch_eo_half(s->prec, op->n, a, stream));
+      a.out_par = 0;  // rhs = D_ee^{-1} (r_e - D_eo t_o)
+      a.v = eo_to;
+      a.z = eo_re;
+      a.y = s->r;
+      TRY(launch_eo_half(s->prec, op->n, a, stream));
+      const double target = fmax(p->inner_tol, 0.5 * p->tol * bn / rn);
+      TRY(s->inner(target, p->max_restarts, m, k, p->recycle_updates, &ii));
+      a.out_par = 1;  // e_o = t_o - D_oo^{-1} D_oe e_e
+      a.v = s->e;
+      a.z = nullptr;
+      a.base = eo_to;
+      a.y = eo_eo;
+      TRY(launch_eo_half(s->prec, op->n, a, stream));
+      TRY(launch_eo_merge(0, s->e, eo_eo, op->eo_sites, op->V, op->n, eo_full, stream));
+      TRY(launch_add_low(x64, op->norms, eo_full, N, stream));
     } else {
       TRY(launch_to_low(r64, op->norms, (float2*)s->r, N, stream));
       const double target = fmax(p->inner_tol, 0.5 * p->tol * bn / rn);

@@ -70,6 +70,10 @@ struct Solver {
   // `prec`); the recycle space belongs to the preconditioned operator of `rec_poly_prec`
   int poly_prec = COARSE_PREC_FP32;
   int rec_poly_prec = -1;
+  // odd-even: the Krylov operator is S = 1 - D_ee^{-1} D_eo D_oo^{-1} D_oe on the even sites
+  // (N = V n / 2); eo_t is the odd-site scratch of its half applies
+  int eo = 0;
+  void* eo_t = nullptr;
   void harvest(int steps_done);     // after a stream sync: add the elapsed time of the applies that ran
 
   ~Solver();
@@ -96,6 +100,6 @@ struct Solver {
 int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, const coarse_solve_params* p,
                  coarse_solve_info* info, cudaStream_t stream, int mu_sign);
 
-Solver* get_solver(coarse_op* op, int prec, int adjoint_system, cudaStream_t stream);
+Solver* get_solver(coarse_op* op, int prec, int adjoint_system, cudaStream_t stream, int odd_even = 0);
 
 }  // namespace coarse

@@ -103,6 +103,16 @@ class CoarseOp:
         check(fn(self.handle, _ptr(x), _ptr(y), nrhs, precision, _stream(stream)))
         return y
 
+    def schur(self, x: torch.Tensor, precision: int = _abi.PREC_FP64, stream=None) -> torch.Tensor:
+        """y = S x, S = 1 - D_ee^{-1} D_eo D_oo^{-1} D_oe on the even sites (x: V/2 * n entries)."""
+        dt = _PREC_DT[precision]
+        if not x.is_cuda or x.dtype != dt or x.numel() != self.V * self.n // 2:
+            raise ValueError(f"expected a CUDA tensor of {self.V * self.n // 2} entries of dtype {dt}")
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        check(lib().coarse_schur_apply(self.handle, _ptr(x), _ptr(y), precision, _stream(stream)))
+        return y
+
     def residual(self, b: torch.Tensor, x: torch.Tensor, stream=None):
         b, _ = self._vec(b, torch.complex128)
         x, _ = self._vec(x, torch.complex128)
