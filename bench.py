@@ -413,6 +413,52 @@ def run_apply_only(args):
     cop.close()
 
 
+def run_schur_only(args):
+    """Odd-even reduced operator S = 1 - D_ee^-1 D_eo D_oo^-1 D_oe alone (two half passes): achieved
+    algorithmic GB/s with an L2 flush (256 MB write) between launches."""
+    import torch
+
+    import paper_2205_09104_gb300 as cg
+    from synthetic.coarse_op import build_coarse_operator
+    fine, nv, m0, mu, desc = APPLY_CASES[args.schur_only]
+    prec = {"fp64": cg.PREC_FP64, "fp32": cg.PREC_FP32, "bf16": cg.PREC_BF16}[args.prec]
+    dev = torch.device("cuda", 0)
+    op = build_coarse_operator((3, 0), fine, nv, m0, CSW, device=dev)
+    cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, mu=mu, precisions=(prec,) if prec else ())
+    del op
+    torch.cuda.empty_cache()
+    n, V = 2 * nv, cop.V
+    N = n * V
+    dt = torch.complex128 if prec == cg.PREC_FP64 else torch.complex64
+    g = torch.Generator(device="cpu").manual_seed(5)
+    x = torch.randn(N // 2, dtype=dt, generator=g).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        cop.schur(x, precision=prec)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        if not args.no_flush:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cop.schur(x, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    esize = {cg.PREC_FP64: 16, cg.PREC_FP32: 8, cg.PREC_BF16: 4}[prec]
+    vsize = 16 if prec == cg.PREC_FP64 else 8
+    nbytes = 9 * n * n * V * esize + 2.5 * N * vsize
+    med = statistics.median(ts)
+    peak, src = peaks()
+    print(json.dumps({"mode": "schur", "case": args.schur_only, "workload": desc, "precision": args.prec,
+                      "l2_flush": not args.no_flush, "median_us": round(med * 1e3, 2), "min_us": round(min(ts) * 1e3, 2),
+                      "bytes_per_launch": int(nbytes), "achieved_gbs": round(nbytes / (med * 1e-3) / 1e9, 1),
+                      "peak_gbs": peak, "frac": round(nbytes / (med * 1e-3) / 1e9 / peak, 4), "peak_source": src,
+                      "launches": len(ts)}), flush=True)
+    cop.close()
+
+
 def run_mrhs(args):
     """Multi-right-hand-side BF16 apply on tensor cores vs one single-column BF16 apply per column:
     coarse 4^4 / 6^4 / 8^4 (V = 256, 1296, 4096), n = 16 / 32 / 48, 1-12 columns; L2 flushed
@@ -543,6 +589,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--apply-only", choices=sorted(APPLY_CASES), default=None,
                     help="time the stencil apply alone on one of the named lattices")
+    ap.add_argument("--schur-only", choices=sorted(APPLY_CASES), default=None,
+                    help="time the odd-even reduced operator alone on one of the named lattices")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--fp64-baseline-steps", type=int, default=2,
                     help="plain FP64 GMRES(50) solves timed for the speedup (0 = skip)")
@@ -558,6 +606,9 @@ def main():
         return
     if args.mrhs:
         run_mrhs(args)
+        return
+    if args.schur_only:
+        run_schur_only(args)
         return
     if args.apply_only:
         run_apply_only(args)

@@ -8,14 +8,17 @@
 // backward hop is the neighbour's forward block, as for the full stencil), with the epilogue
 // y = u, or y = base - u followed by the polynomial-chain step.  B_x = A_x + i mu sigma3 are
 // the diagonal blocks; their inverses are computed once in FP64 (Gauss-Jordan with partial
-// pivoting, one CTA per site) and stored per precision.  Each output site's warp reads its 4
-// forward blocks, its 4 neighbours' forward blocks and its inverse block: every stored block
-// once per half apply, twice per S apply.
+// pivoting, one CTA per site) and stored per precision.  Each output site reads its 4
+// forward blocks, its 4 neighbours' forward blocks and its inverse block (one CTA of 4 warps per
+// site, one warp per direction): every stored block once per half apply, twice per S apply.
+#include <algorithm>
+#include <cstdio>
 #include <vector>
 
 #include "apply_core.cuh"
 #include "common.cuh"
 #include "oddeven.cuh"
+#include "tune.cuh"
 
 namespace coarse {
 namespace {
@@ -105,8 +108,170 @@ __global__ void k_inv_convert(const double2* __restrict__ in, size_t total, floa
 }
 
 // ------------------------------------------------------------------------- the half apply
+// One CTA of 4 warps per output site x: warp mu computes the forward hop F_{x,mu} v_{x+mu} (row
+// sums) and the backward hop sigma3 F_{x-mu,mu}^H sigma3 v_{x-mu} (column sums) into its own
+// slot; h is the sum of the 4 slots in fixed order (deterministic); the inverse block's rows are
+// split over the warps; the epilogue runs over the CTA, coalesced.
 template <int N, class BT, class VT, class AC>
 __global__ void __launch_bounds__(128) k_eo_half(EoArgs a) {
+  constexpr int CPL = N / 8, KR = N / 4, NV = N / 2, KW = KR / 4;  // KW row quads per warp
+  constexpr size_t BSZ = (size_t)N * N;
+  using AT = decltype(AC{}.x);
+  __shared__ AC hpart[4][N];
+  __shared__ AC us[N];
+  const int mu = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 3, t = lane & 7;
+  const int k = blockIdx.x;
+  if (k >= a.V / 2) return;  // CTA-uniform
+  if (a.stop && *a.stop) return;
+  const int x = __ldg(a.sites + a.out_par * (a.V / 2) + k);
+  const BT* B = static_cast<const BT*>(a.blocks);
+  const VT* v = static_cast<const VT*>(a.v);
+  const AT st = (t * CPL < NV) ? AT(1) : AT(-1);  // sigma3 of this lane's columns
+
+  AC yf[KR], yb[CPL];
+#pragma unroll
+  for (int r = 0; r < KR; ++r) yf[r] = AC{0, 0};
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) yb[c] = AC{0, 0};
+  if (v) {
+    // forward hop: row sums of F_{x,mu} v_{x+mu}
+    const int fsrc = __ldg(a.half + __ldg(a.nb + x * 8 + mu));
+    const int nbx = __ldg(a.nb + x * 8 + 4 + mu);
+    const int bsrc = __ldg(a.half + nbx);
+    AC w[CPL], xr[KR];
+    load_vec<VT, AC, CPL>(v + (size_t)fsrc * N + t * CPL, w);
+#pragma unroll
+    for (int r = 0; r < KR; ++r) {
+      const VT vv = v[(size_t)bsrc * N + 4 * r + g];
+      const AT sk = (4 * r + g < NV) ? AT(1) : AT(-1);
+      xr[r].x = sk * AT(vv.x);
+      xr[r].y = sk * AT(vv.y);
+    }
+    const BT* fb = B + ((size_t)x * 5 + 1 + mu) * BSZ + g * N + t * CPL;
+    const BT* bb = B + ((size_t)nbx * 5 + 1 + mu) * BSZ + g * N + t * CPL;
+#pragma unroll
+    for (int r = 0; r < KR; ++r) {
+      AC e[CPL], f[CPL];
+      LoadS<AC, BT>::template row<CPL>(fb + (size_t)r * 4 * N, e);
+      LoadS<AC, BT>::template row<CPL>(bb + (size_t)r * 4 * N, f);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        cfma(yf[r], e[c], w[c]);
+        cfma_conj(yb[c], f[c], xr[r]);  // backward: column sums of conj(F) (sigma3 v)
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < KR; ++r)
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {
+      yf[r].x += __shfl_xor_sync(0xffffffffu, yf[r].x, off);
+      yf[r].y += __shfl_xor_sync(0xffffffffu, yf[r].y, off);
+    }
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int off = 8; off < 32; off <<= 1) {
+      yb[c].x += __shfl_xor_sync(0xffffffffu, yb[c].x, off);
+      yb[c].y += __shfl_xor_sync(0xffffffffu, yb[c].y, off);
+    }
+  AC* hp = hpart[mu];
+  if (t == 0)
+#pragma unroll
+    for (int r = 0; r < KR; ++r) hp[4 * r + g] = yf[r];
+  __syncwarp();
+  if (g == 0)
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) hp[t * CPL + c] = cadd(hp[t * CPL + c], cscale(yb[c], st));
+  __syncthreads();
+  // g = z - h (or h), h = sum of the 4 direction slots: this lane's column chunk
+  AC gi[CPL];
+  const VT* z = static_cast<const VT*>(a.z);
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int j = t * CPL + c;
+    const AC hv = cadd(cadd(hpart[0][j], hpart[1][j]), cadd(hpart[2][j], hpart[3][j]));
+    if (z) {
+      const VT zv = z[(size_t)k * N + j];
+      gi[c] = AC{AT(zv.x) - hv.x, AT(zv.y) - hv.y};
+    } else {
+      gi[c] = hv;
+    }
+  }
+  // u = B_x^{-1} g: warp mu takes the row quads mu*KW .. mu*KW + KW - 1
+  {
+    AC uf[KW];
+#pragma unroll
+    for (int q = 0; q < KW; ++q) uf[q] = AC{0, 0};
+    const BT* blk = static_cast<const BT*>(a.inv) + (size_t)x * BSZ + g * N + t * CPL;
+#pragma unroll
+    for (int q = 0; q < KW; ++q) {
+      AC e[CPL];
+      LoadS<AC, BT>::template row<CPL>(blk + (size_t)(mu * KW + q) * 4 * N, e);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) cfma(uf[q], e[c], gi[c]);
+    }
+#pragma unroll
+    for (int q = 0; q < KW; ++q)
+#pragma unroll
+      for (int off = 1; off < 8; off <<= 1) {
+        uf[q].x += __shfl_xor_sync(0xffffffffu, uf[q].x, off);
+        uf[q].y += __shfl_xor_sync(0xffffffffu, uf[q].y, off);
+      }
+    if (t == 0)
+#pragma unroll
+      for (int q = 0; q < KW; ++q) us[4 * (mu * KW + q) + g] = uf[q];
+  }
+  __syncthreads();
+  // epilogue over the CTA, coalesced: y = u or base - u, then the chain step with x = base
+  const VT* base = static_cast<const VT*>(a.base);
+  VT* y = static_cast<VT*>(a.y);
+  const double2 c0d = a.mode != APPLY_PLAIN ? a.coef[0] : make_double2(0.0, 0.0);
+  const double2 c1d = a.mode != APPLY_PLAIN ? a.coef[1] : make_double2(0.0, 0.0);
+  const double2 c2d = a.mode == APPLY_POLY_FIRST ? a.coef[2] : make_double2(0.0, 0.0);
+  const AC c0{AT(c0d.x), AT(c0d.y)}, c1{AT(c1d.x), AT(c1d.y)}, c2{AT(c2d.x), AT(c2d.y)};
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const size_t idx = (size_t)k * N + e;
+    AC r = us[e];
+    AC xs{0, 0};
+    if (base) {
+      const VT bv = base[idx];
+      xs = AC{AT(bv.x), AT(bv.y)};
+      r = csub(xs, r);
+    }
+    if (a.mode == APPLY_PLAIN) {
+      VT o;
+      o.x = r.x;
+      o.y = r.y;
+      y[idx] = o;
+    } else {
+      // chain step on S: s' = x - c0 (S x) ; acc = acc + c1 s'  (first: acc = c2 x + c1 s')
+      VT* accp = static_cast<VT*>(a.acc) + idx;
+      AC ac;
+      if (a.mode == APPLY_POLY_FIRST) {
+        ac = cmul(c2, xs);
+      } else {
+        const VT av = *accp;
+        ac = AC{AT(av.x), AT(av.y)};
+      }
+      const AC sp = csub(xs, cmul(c0, r));
+      ac = cadd(ac, cmul(c1, sp));
+      VT o;
+      o.x = sp.x;
+      o.y = sp.y;
+      y[idx] = o;
+      VT ao;
+      ao.x = ac.x;
+      ao.y = ac.y;
+      *accp = ao;
+    }
+  }
+}
+
+// Warp-per-site variant (4 sites per CTA): one warp walks all 9 blocks of its site.
+template <int N, class BT, class VT, class AC>
+__global__ void __launch_bounds__(128) k_eo_half_w(EoArgs a) {
   constexpr int CPL = N / 8, KR = N / 4, NV = N / 2;
   constexpr size_t BSZ = (size_t)N * N;
   using AT = decltype(AC{}.x);
@@ -356,26 +521,85 @@ int eo_prepare(coarse_op* op, double mu_eff, cudaStream_t s) {
   return COARSE_OK;
 }
 
-int launch_eo_half(int prec, int n, const EoArgs& a, cudaStream_t s) {
+namespace {
+
+template <class BT, class VT, class AC>
+int launch_eo_variant(int variant, int n, const EoArgs& a, cudaStream_t s) {
   const int half = a.V / 2;
-  if (half <= 0) return COARSE_OK;
-  const dim3 grid((half + 3) / 4), block(128);
-#define EO_CASE(NN)                                                                                       \
-  case NN:                                                                                                \
-    if (prec == COARSE_PREC_FP64) k_eo_half<NN, double2, double2, double2><<<grid, block, 0, s>>>(a);    \
-    else if (prec == COARSE_PREC_FP32) k_eo_half<NN, float2, float2, float2><<<grid, block, 0, s>>>(a);  \
-    else k_eo_half<NN, cbf16, float2, float2><<<grid, block, 0, s>>>(a);                                 \
-    break;
+  const dim3 block(128);
+  const dim3 grid = variant == 1 ? dim3((half + 3) / 4) : dim3(half);
   switch (n) {
-    EO_CASE(16)
-    EO_CASE(32)
-    EO_CASE(48)
+    case 16: variant == 1 ? k_eo_half_w<16, BT, VT, AC><<<grid, block, 0, s>>>(a) : k_eo_half<16, BT, VT, AC><<<grid, block, 0, s>>>(a); break;
+    case 32: variant == 1 ? k_eo_half_w<32, BT, VT, AC><<<grid, block, 0, s>>>(a) : k_eo_half<32, BT, VT, AC><<<grid, block, 0, s>>>(a); break;
+    case 48: variant == 1 ? k_eo_half_w<48, BT, VT, AC><<<grid, block, 0, s>>>(a) : k_eo_half<48, BT, VT, AC><<<grid, block, 0, s>>>(a); break;
     default: set_error("odd-even: unsupported n = %d", n); return COARSE_ERR_INVALID_ARG;
   }
-#undef EO_CASE
   note_launch();
   COARSE_CUDA(cudaGetLastError());
   return COARSE_OK;
+}
+
+// The autotuner picks, per (precision, n, lattice-size bucket), between one CTA of 4 warps per
+// site (candidate 0) and one warp per site (candidate 1); candidates run in plain mode into a
+// scratch output.
+template <class BT, class VT, class AC>
+int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
+  static int choice[3][32];
+  static bool init = false;
+  if (!init) {
+    for (auto& row : choice)
+      for (int& c : row) c = -1;
+    init = true;
+  }
+  const int ni = n / 16 - 1, vb = std::min(tune_bucket(a.V), 31);
+  if (ni < 0 || ni > 2) {
+    set_error("odd-even: unsupported n = %d", n);
+    return COARSE_ERR_INVALID_ARG;
+  }
+  if (choice[ni][vb] < 0) {
+    char key[64];
+    snprintf(key, sizeof(key), "eo/p%d/n%d/v%d", prec, n, vb);
+    void* scratch = nullptr;
+    auto run = [&](const TuneChoice& c) -> int {
+      if (!scratch && cudaMalloc(&scratch, sizeof(VT) * (size_t)(a.V / 2) * n) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("odd-even: autotuner scratch allocation failed");
+        return COARSE_ERR_OOM;
+      }
+      EoArgs t = a;
+      t.mode = APPLY_PLAIN;
+      t.y = scratch;
+      t.acc = nullptr;
+      t.coef = nullptr;
+      t.stop = nullptr;
+      return launch_eo_variant<BT, VT, AC>(c.a, n, t, s);
+    };
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    TuneChoice c;
+    const int rc = tune_pick(key, {TuneChoice{0, 0, 0}, TuneChoice{1, 0, 0}}, run, s, &c);
+    if (scratch) {
+      cudaStreamSynchronize(s);
+      cudaFree(scratch);
+    }
+    if (rc != COARSE_OK) return rc;
+    if (cap != cudaStreamCaptureStatusNone) return launch_eo_variant<BT, VT, AC>(c.a, n, a, s);
+    choice[ni][vb] = c.a;
+  }
+  return launch_eo_variant<BT, VT, AC>(choice[ni][vb], n, a, s);
+}
+
+}  // namespace
+
+int launch_eo_half(int prec, int n, const EoArgs& a, cudaStream_t s) {
+  if (a.V / 2 <= 0) return COARSE_OK;
+  switch (prec) {
+    case COARSE_PREC_FP64: return launch_eo_tuned<double2, double2, double2>(prec, n, a, s);
+    case COARSE_PREC_FP32: return launch_eo_tuned<float2, float2, float2>(prec, n, a, s);
+    case COARSE_PREC_BF16: return launch_eo_tuned<cbf16, float2, float2>(prec, n, a, s);
+  }
+  set_error("odd-even: unknown precision %d", prec);
+  return COARSE_ERR_INVALID_ARG;
 }
 
 int launch_eo_split(int v64, const void* full, const int* sites, int V, int n, void* ev, void* od, cudaStream_t s) {
