@@ -103,16 +103,15 @@ class ClockSampler:
 
 
 def dist_init():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2205_09104_gb300.replicas import dist_env
+    return dist_env()
 
 
 def run_gb300(args):
     import torch
 
     import paper_2205_09104_gb300 as cg
+    from paper_2205_09104_gb300 import replicas
     from synthetic import draws
     from synthetic.coarse_op import build_coarse_operator
 
@@ -137,7 +136,7 @@ def run_gb300(args):
     n, V = 2 * NV, cop.V
     N = V * n
     total = args.warmup + 2 * args.steps
-    B = torch.from_numpy(draws.rhs((*KEY, 100 + rank), total, N)).to(dev)
+    B = torch.from_numpy(draws.rhs(replicas.rhs_key(KEY, rank), total, N)).to(dev)
     S = torch.from_numpy(draws.rhs((*KEY, 50 + rank), 4, N)).to(dev)  # setup right-hand sides
     X = torch.zeros_like(B)
     # FP32 inner solves to 2e-6: two refinement steps reach 1e-10 ((2e-6)^2 with margin)
@@ -177,13 +176,8 @@ def run_gb300(args):
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), dev)
+    value = replicas.job_rate(args.steps, world, ms)
     worst_res = max(i["rel_residual"] for i in infos)
     # end to end: pinned host b -> device, solve, device x -> pinned host, every step
     hb = B[args.warmup + args.steps:].cpu().pin_memory()
@@ -200,12 +194,7 @@ def run_gb300(args):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = replicas.max_over_ranks(e0.elapsed_time(e1), dev)
     # roofline of the stencil apply (the dominant kernel): algorithmic bytes of every timed launch
     # (5 n^2 V block bytes of its precision + 2 N vector bytes) over their summed device time
     apply_ms = sum(i["apply_ms"] for i in infos)
@@ -235,7 +224,7 @@ def run_gb300(args):
                    "inner_system": ("odd-even reduced, block-Jacobi preconditioned S = 1 - D_ee^-1 D_eo D_oo^-1 D_oe"
                                     if args.oddeven == "on" else "full coarse operator"),
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": round(world * args.steps / (ms_e2e / 1e3), 3), "unit": "solves/s",
+        "e2e": {"value": round(replicas.job_rate(args.steps, world, ms_e2e), 3), "unit": "solves/s",
                 "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
         "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
