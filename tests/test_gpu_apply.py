@@ -1,6 +1,6 @@
 """GPU parity of the coarse stencil apply (Sec. 2.2) against the FP64 oracle, through the C ABI.
 
-Tolerances (derived from the arithmetic, see DESIGN.md):
+Tolerances (derived from the arithmetic):
   FP64 blocks, FP64 accumulation : 1e-12 relative (norm-wise)
   FP32 blocks, FP32 accumulation : 2e-6 relative (9n-term sums of products rounded to 2^-24)
   BF16 blocks, FP32 accumulation : 1e-2 relative (entries rounded to 2^-9, random-sign sums)

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # coarse lattices of 16, 36 and 81 sites (buckets 4, 5, 6) from fine lattices of twice the extent
 FINE = ["4x4x4x4", "6x4x4x6", "6x6x6x6"]
 BUCKETS = [4, 5, 6]
-CONFIGS = {  # nv: (P, S) per bucket
+LAYOUTS = {  # nv: (P, S) per bucket
     8: [(2, 3), (4, 5), (8, 8)],
     16: [(1, 3), (2, 5), (4, 8)],
     24: [(1, 8), (2, 3), (1, 5)],
@@ -26,7 +26,7 @@ def test_mrhs_every_config(tmp_path, nv):
     n = 2 * nv
     cache = tmp_path / "tune.txt"
     with open(cache, "w") as f:
-        for b, (P, S) in zip(BUCKETS, CONFIGS[nv]):
+        for b, (P, S) in zip(BUCKETS, LAYOUTS[nv]):
             for t in (1, 2, 3):
                 f.write(f"mrhs/n{n}/t{t}/v{b} {P} {S} 0 0\n")
     env = dict(os.environ, COARSE_AUTOTUNE_CACHE=str(cache))
@@ -36,5 +36,5 @@ def test_mrhs_every_config(tmp_path, nv):
                           "2,7,12"], env=env, cwd=root, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-4000:]
     assert out.stdout.strip().endswith("ok")
-    for b, (P, S) in zip(BUCKETS, CONFIGS[nv]):
+    for b, (P, S) in zip(BUCKETS, LAYOUTS[nv]):
         assert f"mrhs/n{n}/t3/v{b} -> {P} {S} 0" in out.stdout
