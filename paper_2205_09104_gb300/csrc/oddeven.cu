@@ -9,8 +9,8 @@
 // y = u, or y = base - u followed by the polynomial-chain step.  B_x = A_x + i mu sigma3 are
 // the diagonal blocks; their inverses are computed once in FP64 (Gauss-Jordan with partial
 // pivoting, one CTA per site) and stored per precision.  Each output site reads its 4
-// forward blocks, its 4 neighbours' forward blocks and its inverse block (one CTA of 4 warps per
-// site, one warp per direction): every stored block once per half apply, twice per S apply.
+// forward blocks, its 4 neighbours' forward blocks and its inverse block: every stored block
+// once per half apply, twice per S apply.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
@@ -108,18 +108,19 @@ __global__ void k_inv_convert(const double2* __restrict__ in, size_t total, floa
 }
 
 // ------------------------------------------------------------------------- the half apply
-// One CTA of 4 warps per output site x: warp mu computes the forward hop F_{x,mu} v_{x+mu} (row
-// sums) and the backward hop sigma3 F_{x-mu,mu}^H sigma3 v_{x-mu} (column sums) into its own
-// slot; h is the sum of the 4 slots in fixed order (deterministic); the inverse block's rows are
-// split over the warps; the epilogue runs over the CTA, coalesced.
-template <int N, class BT, class VT, class AC>
-__global__ void __launch_bounds__(128) k_eo_half(EoArgs a) {
-  constexpr int CPL = N / 8, KR = N / 4, NV = N / 2, KW = KR / 4;  // KW row quads per warp
+// One CTA of W warps (W = 4 or 2) per output site x: warp w computes, for its directions
+// mu = w, w + W, ..., the forward hop F_{x,mu} v_{x+mu} (row sums) and the backward hop
+// sigma3 F_{x-mu,mu}^H sigma3 v_{x-mu} (column sums) into its own slot; h is the sum of the W
+// slots in fixed order (deterministic); the inverse block's rows are split over the warps; the
+// epilogue runs over the CTA, coalesced.
+template <int N, class BT, class VT, class AC, int W>
+__global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
+  constexpr int CPL = N / 8, KR = N / 4, NV = N / 2, KW = KR / W;  // KW row quads per warp
   constexpr size_t BSZ = (size_t)N * N;
   using AT = decltype(AC{}.x);
-  __shared__ AC hpart[4][N];
+  __shared__ AC hpart[W][N];
   __shared__ AC us[N];
-  const int mu = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 3, t = lane & 7;
   const int k = blockIdx.x;
   if (k >= a.V / 2) return;  // CTA-uniform
@@ -135,30 +136,33 @@ __global__ void __launch_bounds__(128) k_eo_half(EoArgs a) {
 #pragma unroll
   for (int c = 0; c < CPL; ++c) yb[c] = AC{0, 0};
   if (v) {
-    // forward hop: row sums of F_{x,mu} v_{x+mu}
-    const int fsrc = __ldg(a.half + __ldg(a.nb + x * 8 + mu));
-    const int nbx = __ldg(a.nb + x * 8 + 4 + mu);
-    const int bsrc = __ldg(a.half + nbx);
-    AC w[CPL], xr[KR];
-    load_vec<VT, AC, CPL>(v + (size_t)fsrc * N + t * CPL, w);
+#pragma unroll 1
+    for (int mu = wid; mu < 4; mu += W) {
+      // forward hop: row sums of F_{x,mu} v_{x+mu}; backward: column sums of conj(F_{x-mu,mu}) (sigma3 v)
+      const int fsrc = __ldg(a.half + __ldg(a.nb + x * 8 + mu));
+      const int nbx = __ldg(a.nb + x * 8 + 4 + mu);
+      const int bsrc = __ldg(a.half + nbx);
+      AC w[CPL], xr[KR];
+      load_vec<VT, AC, CPL>(v + (size_t)fsrc * N + t * CPL, w);
 #pragma unroll
-    for (int r = 0; r < KR; ++r) {
-      const VT vv = v[(size_t)bsrc * N + 4 * r + g];
-      const AT sk = (4 * r + g < NV) ? AT(1) : AT(-1);
-      xr[r].x = sk * AT(vv.x);
-      xr[r].y = sk * AT(vv.y);
-    }
-    const BT* fb = B + ((size_t)x * 5 + 1 + mu) * BSZ + g * N + t * CPL;
-    const BT* bb = B + ((size_t)nbx * 5 + 1 + mu) * BSZ + g * N + t * CPL;
+      for (int r = 0; r < KR; ++r) {
+        const VT vv = v[(size_t)bsrc * N + 4 * r + g];
+        const AT sk = (4 * r + g < NV) ? AT(1) : AT(-1);
+        xr[r].x = sk * AT(vv.x);
+        xr[r].y = sk * AT(vv.y);
+      }
+      const BT* fb = B + ((size_t)x * 5 + 1 + mu) * BSZ + g * N + t * CPL;
+      const BT* bb = B + ((size_t)nbx * 5 + 1 + mu) * BSZ + g * N + t * CPL;
 #pragma unroll
-    for (int r = 0; r < KR; ++r) {
-      AC e[CPL], f[CPL];
-      LoadS<AC, BT>::template row<CPL>(fb + (size_t)r * 4 * N, e);
-      LoadS<AC, BT>::template row<CPL>(bb + (size_t)r * 4 * N, f);
+      for (int r = 0; r < KR; ++r) {
+        AC e[CPL], f[CPL];
+        LoadS<AC, BT>::template row<CPL>(fb + (size_t)r * 4 * N, e);
+        LoadS<AC, BT>::template row<CPL>(bb + (size_t)r * 4 * N, f);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        cfma(yf[r], e[c], w[c]);
-        cfma_conj(yb[c], f[c], xr[r]);  // backward: column sums of conj(F) (sigma3 v)
+        for (int c = 0; c < CPL; ++c) {
+          cfma(yf[r], e[c], w[c]);
+          cfma_conj(yb[c], f[c], xr[r]);
+        }
       }
     }
   }
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(128) k_eo_half(EoArgs a) {
       yb[c].x += __shfl_xor_sync(0xffffffffu, yb[c].x, off);
       yb[c].y += __shfl_xor_sync(0xffffffffu, yb[c].y, off);
     }
-  AC* hp = hpart[mu];
+  AC* hp = hpart[wid];
   if (t == 0)
 #pragma unroll
     for (int r = 0; r < KR; ++r) hp[4 * r + g] = yf[r];
@@ -191,7 +195,9 @@ __global__ void __launch_bounds__(128) k_eo_half(EoArgs a) {
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
     const int j = t * CPL + c;
-    const AC hv = cadd(cadd(hpart[0][j], hpart[1][j]), cadd(hpart[2][j], hpart[3][j]));
+    AC hv = hpart[0][j];
+#pragma unroll
+    for (int q = 1; q < W; ++q) hv = cadd(hv, hpart[q][j]);
     if (z) {
       const VT zv = z[(size_t)k * N + j];
       gi[c] = AC{AT(zv.x) - hv.x, AT(zv.y) - hv.y};
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(128) k_eo_half(EoArgs a) {
       gi[c] = hv;
     }
   }
-  // u = B_x^{-1} g: warp mu takes the row quads mu*KW .. mu*KW + KW - 1
+  // u = B_x^{-1} g: warp w takes the row quads w*KW .. w*KW + KW - 1
   {
     AC uf[KW];
 #pragma unroll
@@ -208,7 +214,7 @@ __global__ void __launch_bounds__(128) k_eo_half(EoArgs a) {
 #pragma unroll
     for (int q = 0; q < KW; ++q) {
       AC e[CPL];
-      LoadS<AC, BT>::template row<CPL>(blk + (size_t)(mu * KW + q) * 4 * N, e);
+      LoadS<AC, BT>::template row<CPL>(blk + (size_t)(wid * KW + q) * 4 * N, e);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) cfma(uf[q], e[c], gi[c]);
     }
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(128) k_eo_half(EoArgs a) {
       }
     if (t == 0)
 #pragma unroll
-      for (int q = 0; q < KW; ++q) us[4 * (mu * KW + q) + g] = uf[q];
+      for (int q = 0; q < KW; ++q) us[4 * (wid * KW + q) + g] = uf[q];
   }
   __syncthreads();
   // epilogue over the CTA, coalesced: y = u or base - u, then the chain step with x = base
@@ -526,22 +532,27 @@ namespace {
 template <class BT, class VT, class AC>
 int launch_eo_variant(int variant, int n, const EoArgs& a, cudaStream_t s) {
   const int half = a.V / 2;
-  const dim3 block(128);
-  const dim3 grid = variant == 1 ? dim3((half + 3) / 4) : dim3(half);
+#define EO_LAUNCH(NN)                                                                           \
+  case NN:                                                                                      \
+    if (variant == 1) k_eo_half_w<NN, BT, VT, AC><<<(half + 3) / 4, 128, 0, s>>>(a);             \
+    else if (variant == 2) k_eo_half<NN, BT, VT, AC, 2><<<half, 64, 0, s>>>(a);                  \
+    else k_eo_half<NN, BT, VT, AC, 4><<<half, 128, 0, s>>>(a);                                   \
+    break;
   switch (n) {
-    case 16: variant == 1 ? k_eo_half_w<16, BT, VT, AC><<<grid, block, 0, s>>>(a) : k_eo_half<16, BT, VT, AC><<<grid, block, 0, s>>>(a); break;
-    case 32: variant == 1 ? k_eo_half_w<32, BT, VT, AC><<<grid, block, 0, s>>>(a) : k_eo_half<32, BT, VT, AC><<<grid, block, 0, s>>>(a); break;
-    case 48: variant == 1 ? k_eo_half_w<48, BT, VT, AC><<<grid, block, 0, s>>>(a) : k_eo_half<48, BT, VT, AC><<<grid, block, 0, s>>>(a); break;
+    EO_LAUNCH(16)
+    EO_LAUNCH(32)
+    EO_LAUNCH(48)
     default: set_error("odd-even: unsupported n = %d", n); return COARSE_ERR_INVALID_ARG;
   }
+#undef EO_LAUNCH
   note_launch();
   COARSE_CUDA(cudaGetLastError());
   return COARSE_OK;
 }
 
 // The autotuner picks, per (precision, n, lattice-size bucket), between one CTA of 4 warps per
-// site (candidate 0) and one warp per site (candidate 1); candidates run in plain mode into a
-// scratch output.
+// site (candidate 0), one warp per site (candidate 1) and one CTA of 2 warps per site
+// (candidate 2); candidates run in plain mode into a scratch output.
 template <class BT, class VT, class AC>
 int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
   static int choice[3][32];
@@ -577,7 +588,7 @@ int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     TuneChoice c;
-    const int rc = tune_pick(key, {TuneChoice{0, 0, 0}, TuneChoice{1, 0, 0}}, run, s, &c);
+    const int rc = tune_pick(key, {TuneChoice{0, 0, 0}, TuneChoice{1, 0, 0}, TuneChoice{2, 0, 0}}, run, s, &c);
     if (scratch) {
       cudaStreamSynchronize(s);
       cudaFree(scratch);
