@@ -49,6 +49,7 @@ struct __align__(4) cbf16 { __nv_bfloat16 x, y; };
 // ------------------------------------------------------------------ error state
 void set_error(const char* fmt, ...);
 void note_launch();          // counts kernels launched by the library
+void note_launches(long long n);  // ... n at once (kernels of a replayed CUDA graph)
 int sm_count();              // multiprocessors of the current device (cached)
 long long launches_so_far();
 int cuda_fail(cudaError_t e, const char* what);

@@ -42,7 +42,89 @@ int dalloc(T** p, size_t count) {
 
 Solver::~Solver() { release(); }
 
+void Solver::clear_graphs() {
+  for (auto& kv : graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (const Timed& tm : kv.second.timed_tpl) {
+      ev_pool.push_back(tm.a);
+      ev_pool.push_back(tm.b);
+    }
+  }
+  graphs.clear();
+  // replayed entries of graph-owned events may still sit in `timed`: their events went back above
+  std::vector<Timed> keep;
+  for (const Timed& tm : timed)
+    if (!tm.graph_owned) keep.push_back(tm);
+  timed.swap(keep);
+  cycles_done = 0;
+}
+
+// Steps j0 .. j0+cnt-1 of the current cycle: eager launches for the solver's first cycle and
+// for solves that time their stencil launches (COARSE_TIME_APPLY: per-launch events), otherwise a
+// CUDA graph per (j0, cnt, kc, recycle parity, chain precision, degree) captured once, replayed.
+int Solver::run_chunk(int j0, int cnt, int kc, void* const* tab) {
+  auto issue = [&]() -> int {
+    for (int j = j0; j < j0 + cnt; ++j) {
+      cur_tag = j;
+      TRY(opA(V[j], V[j + 1], &st->stop));
+      TRY(arnoldi_step(j, kc, tab));
+    }
+    return COARSE_OK;
+  };
+  if (cycles_done < 1 || time_apply) return issue();
+  const unsigned long long key = (unsigned long long)j0 | ((unsigned long long)cnt << 8) |
+                                 ((unsigned long long)kc << 16) | ((unsigned long long)par << 24) |
+                                 ((unsigned long long)poly_prec << 26) | ((unsigned long long)d << 28);
+  auto it = graphs.find(key);
+  if (it == graphs.end()) {
+    if (!cap_stream) COARSE_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    ChunkGraph g;
+    const cudaStream_t user = stream;
+    const long long l0 = launches_so_far(), mv0 = matvecs;
+    const size_t t0 = timed.size();
+    stream = cap_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? issue() : cuda_fail(e, "cudaStreamBeginCapture");
+    cudaError_t e2 = cudaStreamEndCapture(cap_stream, &graph);
+    stream = user;
+    if (rc == COARSE_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
+    if (rc == COARSE_OK) {
+      e2 = cudaGraphInstantiate(&g.exec, graph, 0);
+      if (e2 != cudaSuccess) rc = cuda_fail(e2, "cudaGraphInstantiate");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    g.kernels = launches_so_far() - l0;
+    g.matvecs = matvecs - mv0;
+    g.timed_tpl.assign(timed.begin() + t0, timed.end());
+    for (Timed& tm : g.timed_tpl) tm.graph_owned = true;
+    timed.resize(t0);
+    // the capture counted its launches and applies once: they run only when replayed
+    note_launches(-g.kernels);
+    matvecs = mv0;
+    if (rc != COARSE_OK) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      for (const Timed& tm : g.timed_tpl) {
+        ev_pool.push_back(tm.a);
+        ev_pool.push_back(tm.b);
+      }
+      return rc;
+    }
+    it = graphs.emplace(key, std::move(g)).first;
+  }
+  COARSE_CUDA(cudaGraphLaunch(it->second.exec, stream));
+  note_launches(it->second.kernels);
+  matvecs += it->second.matvecs;
+  for (const Timed& tm : it->second.timed_tpl) timed.push_back(tm);
+  return COARSE_OK;
+}
+
 void Solver::release() {
+  clear_graphs();
+  if (cap_stream) {
+    cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
+  }
   for (const Timed& tm : timed) {
     ev_pool.push_back(tm.a);
     ev_pool.push_back(tm.b);
@@ -191,8 +273,10 @@ void Solver::harvest(int steps_done) {
         ++apply_count;
       }
     }
-    ev_pool.push_back(tm.a);
-    ev_pool.push_back(tm.b);
+    if (!tm.graph_owned) {
+      ev_pool.push_back(tm.a);
+      ev_pool.push_back(tm.b);
+    }
   }
   timed.clear();
 }
@@ -246,6 +330,7 @@ int Solver::arnoldi_step(int j, int kc, void* const* tab) {
 }
 
 int Solver::build_poly(const double2* start64, uint64_t seed, int dd) {
+  clear_graphs();  // graphs bake host-side chain constants (theta_1 for degree 1)
   poly_ok = false;
   d = 0;
   if (dd <= 0) { poly_ok = true; return COARSE_OK; }
@@ -312,12 +397,9 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
     int pending = -1;  // chunk whose flag copy is in flight
     int launched = 0;
     for (int j0 = 0; j0 < steps; j0 += kChunk) {
-      for (int j = j0; j < steps && j < j0 + kChunk; ++j) {
-        ++launched;
-        cur_tag = j;
-        TRY(opA(V[j], V[j + 1], &st->stop));
-        TRY(arnoldi_step(j, kc, tab));
-      }
+      const int cnt = steps - j0 < kChunk ? steps - j0 : kChunk;
+      launched += cnt;
+      TRY(run_chunk(j0, cnt, kc, tab));
       const int slot = (j0 / kChunk) & 1;
       COARSE_CUDA(cudaMemcpyAsync(stop_host + slot, &st->stop, sizeof(int), cudaMemcpyDeviceToHost, stream));
       COARSE_CUDA(cudaEventRecord(chunk_ev[slot], stream));
@@ -331,6 +413,7 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
     TRY(read_state());
     const CycleState cs = *st_host;
     harvest(cs.j);
+    ++cycles_done;
     matvecs -= (long long)(launched - cs.j) * (d > 1 ? d : 1);  // gated steps did not run
     info->cycles++;
     if (cs.status & ST_NONFINITE) {

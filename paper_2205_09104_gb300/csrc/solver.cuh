@@ -1,6 +1,8 @@
 // Per-operator, per-precision Krylov solver state (host object owning device memory).
 #pragma once
 
+#include <map>
+
 #include <vector>
 
 #include "common.cuh"
@@ -60,7 +62,7 @@ struct Solver {
   // optional CUDA-event timing of the stencil launches (COARSE_TIME_APPLY)
   bool time_apply = false;
   int cur_tag = -1;                 // Arnoldi step of the applies being launched (-1: not gated)
-  struct Timed { int tag; cudaEvent_t a, b; double bytes; };
+  struct Timed { int tag; cudaEvent_t a, b; double bytes; bool graph_owned = false; };
   std::vector<Timed> timed;         // launched, not yet harvested
   std::vector<cudaEvent_t> ev_pool;
   double apply_ms = 0.0;
@@ -74,6 +76,19 @@ struct Solver {
   // (N = V n / 2); eo_t is the odd-site scratch of its half applies
   int eo = 0;
   void* eo_t = nullptr;
+  // Arnoldi-step chunks captured as CUDA graphs (after the solver's first eager cycle, so that
+  // every autotuner decision is made), replayed for every later cycle with the same shape
+  struct ChunkGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;           // kernels in the graph (launch accounting on replay)
+    long long matvecs = 0;           // operator applies in the graph
+    std::vector<Timed> timed_tpl;    // timing events recorded by the graph's event nodes
+  };
+  std::map<unsigned long long, ChunkGraph> graphs;
+  int cycles_done = 0;
+  cudaStream_t cap_stream = nullptr;
+  void clear_graphs();
+  int run_chunk(int j0, int cnt, int kc, void* const* tab);
   void harvest(int steps_done);     // after a stream sync: add the elapsed time of the applies that ran
 
   ~Solver();
@@ -87,6 +102,7 @@ struct Solver {
   int build_poly(const double2* start64, uint64_t seed, int d);
   int inner(double target_abs, int max_cycles, int m, int kdef, int ulimit, InnerInfo* info);
   void invalidate() {
+    clear_graphs();
     poly_ok = false;
     d = 0;
     k_cur = 0;
