@@ -113,7 +113,7 @@ __global__ void k_inv_convert(const double2* __restrict__ in, size_t total, floa
 // sigma3 F_{x-mu,mu}^H sigma3 v_{x-mu} (column sums) into its own slot; h is the sum of the W
 // slots in fixed order (deterministic); the inverse block's rows are split over the warps; the
 // epilogue runs over the CTA, coalesced.
-template <int N, class BT, class VT, class AC, int W>
+template <int N, class BT, class VT, class AC, int W, bool UNROLL = false>
 __global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
   constexpr int CPL = N / 8, KR = N / 4, NV = N / 2, KW = KR / W;  // KW row quads per warp
   constexpr size_t BSZ = (size_t)N * N;
@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
 #pragma unroll
   for (int c = 0; c < CPL; ++c) yb[c] = AC{0, 0};
   if (v) {
-#pragma unroll 1
+    // UNROLL: the warp's directions are unrolled so that all their block loads are in flight at once
+#pragma unroll (UNROLL ? 4 : 1)
     for (int mu = wid; mu < 4; mu += W) {
       // forward hop: row sums of F_{x,mu} v_{x+mu}; backward: column sums of conj(F_{x-mu,mu}) (sigma3 v)
       const int fsrc = __ldg(a.half + __ldg(a.nb + x * 8 + mu));
@@ -536,6 +537,7 @@ int launch_eo_variant(int variant, int n, const EoArgs& a, cudaStream_t s) {
   case NN:                                                                                      \
     if (variant == 1) k_eo_half_w<NN, BT, VT, AC><<<(half + 3) / 4, 128, 0, s>>>(a);             \
     else if (variant == 2) k_eo_half<NN, BT, VT, AC, 2><<<half, 64, 0, s>>>(a);                  \
+    else if (variant == 3) k_eo_half<NN, BT, VT, AC, 2, true><<<half, 64, 0, s>>>(a);            \
     else k_eo_half<NN, BT, VT, AC, 4><<<half, 128, 0, s>>>(a);                                   \
     break;
   switch (n) {
@@ -551,8 +553,9 @@ int launch_eo_variant(int variant, int n, const EoArgs& a, cudaStream_t s) {
 }
 
 // The autotuner picks, per (precision, n, lattice-size bucket), between one CTA of 4 warps per
-// site (candidate 0), one warp per site (candidate 1) and one CTA of 2 warps per site
-// (candidate 2); candidates run in plain mode into a scratch output.
+// site (candidate 0), one warp per site (candidate 1) and one CTA of 2 warps per site with the
+// direction loop rolled (candidate 2) or unrolled (candidate 3); candidates run in plain mode into
+// a scratch output.
 template <class BT, class VT, class AC>
 int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
   static int choice[3][32];
@@ -588,7 +591,8 @@ int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     TuneChoice c;
-    const int rc = tune_pick(key, {TuneChoice{0, 0, 0}, TuneChoice{1, 0, 0}, TuneChoice{2, 0, 0}}, run, s, &c);
+    const int rc = tune_pick(key, {TuneChoice{0, 0, 0}, TuneChoice{1, 0, 0}, TuneChoice{2, 0, 0}, TuneChoice{3, 0, 0}},
+                             run, s, &c);
     if (scratch) {
       cudaStreamSynchronize(s);
       cudaFree(scratch);

@@ -1,5 +1,6 @@
 """Every layout the autotuner may pick for the odd-even half apply (one CTA of 4 warps per site,
-one warp per site, one CTA of 2 warps per site) gives the oracle's S = 1 - D_ee^-1 D_eo D_oo^-1 D_oe: the layout is fixed
+one warp per site, one CTA of 2 warps per site with rolled or unrolled directions) gives the
+oracle's S = 1 - D_ee^-1 D_eo D_oo^-1 D_oe: the layout is fixed
 through the autotuner's cache file in a subprocess and checked in three precisions."""
 import os
 import subprocess
@@ -13,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CASES = [(8, "8x8x8x8", 0.0), (16, "8x4x4x8", 0.03), (24, "4x8x4x4", 0.0)]  # coarse 4^4, 4x2x2x4, 2x4x2x2
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("nv,fdims,mu", CASES)
 def test_eo_layout(tmp_path, variant, nv, fdims, mu):
     n = 2 * nv
