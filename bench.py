@@ -529,14 +529,16 @@ def run_batched(args):
     ops, bs, xs = [], [], []
     for i, (L, nv, m0, nr) in enumerate(recipe):
         op = build_coarse_operator((4, 1 + i), (2 * L,) * 4, nv, m0, CSW, device=dev)
-        ops.append(cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(prec,), max_nrhs=12))
+        ops.append(cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(prec, cg.PREC_BF16),
+                               max_nrhs=12))
         N = op.volume * op.n
         bs.append(torch.from_numpy(draws.rhs((4, 1 + i, 7), nr, N)).to(dev))
         xs.append(torch.zeros_like(bs[-1]))
         del op
     t_gen = time.perf_counter() - t
     inner_tol = 1e-5 if prec == cg.PREC_FP32 else 1e-2
-    p = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS, **PARAMS)
+    chain = cg.COARSE_POLY_BF16 if (prec == cg.PREC_FP32 and args.poly == "bf16") else 0
+    p = cg.solve_params(precision=prec, inner_tol=inner_tol, flags=cg.COARSE_ZERO_GUESS | chain, **PARAMS)
     t = time.perf_counter()
     cg.solve_batched(ops, bs, xs, p)          # setup (polynomials, recycle spaces) + first batch
     torch.cuda.synchronize()
@@ -563,7 +565,8 @@ def run_batched(args):
     torch.cuda.synchronize()
     ms_seq = e0.elapsed_time(e1)
     print(json.dumps({"mode": "batched", "operators": len(ops), "right_hand_sides": nrhs,
-                      "precision": args.prec, "ms_per_batch": round(ms, 2),
+                      "precision": args.prec, "polynomial_chain_blocks": "bf16" if chain else args.prec,
+                      "ms_per_batch": round(ms, 2),
                       "rhs_solves_per_s": round(nrhs / (ms / 1e3), 1), "operator_batches_per_s": round(1e3 / ms, 3),
                       "sequential_ms": round(ms_seq, 2), "speedup_vs_sequential": round(ms_seq / ms, 2),
                       "worst_rel_residual": worst, "kernel_launches_per_batch": infos[0]["kernel_launches"],

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(128) kb_apply(BApply b) {
   if (!bgate(s, b.gate)) return;  // uniform for all sites of the solve
   const int step = *b.step;
   ApplyArgs a;
-  a.blocks = s.blk;
+  a.blocks = b.poly_blocks ? s.blk_poly : s.blk;
   a.nb = s.nb;
   a.V = s.V;
   a.mu = s.mu;

@@ -15,6 +15,7 @@ constexpr int kBatchMaxQ = 104;  // dots per reduction (equals the chunked kerne
 struct BSolve {
   // operator (shared by the solves of one operator)
   const void* blk;     // inner-precision blocks [V][5][n][n]
+  const void* blk_poly; // blocks of the polynomial-chain phases (BF16 with COARSE_POLY_BF16, else blk)
   const void* blk64;   // FP64 blocks
   const int* nb;       // [V][8]
   int V, n, N;
@@ -75,6 +76,7 @@ struct BApply {
   int coef_off;         // offset (in double2) into polyc for POLY modes
   int gate;             // BGate
   const int* step;      // device step counter
+  int poly_blocks;      // 1: the solves' blk_poly (polynomial-chain phases), 0: blk
 };
 
 // work item -> solve, gates and vector selection shared by the batched kernels

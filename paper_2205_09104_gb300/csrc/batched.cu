@@ -56,6 +56,7 @@ inline void bm_shape(int n, int* P, int* S) {
 
 struct Batch {
   int prec = COARSE_PREC_FP32;
+  int poly_prec = COARSE_PREC_FP32;  // blocks of the polynomial-chain phases
   bool mrhs = false;              // BF16 stencil phases on the tensor-core multi-RHS kernel
   std::vector<MGroup> mgroups;
   BMOp* dops = nullptr;
@@ -90,8 +91,8 @@ struct Batch {
     if (states_h) cudaFreeHost(states_h);
   }
 
-  // one stencil phase over all n-groups
-  int apply_phase(int mode, int xsel, int ysel, int coef_off, int gate, cudaStream_t s) {
+  // one stencil phase over all n-groups (chain: a polynomial-chain phase, on the chain's blocks)
+  int apply_phase(int mode, int xsel, int ysel, int coef_off, int gate, cudaStream_t s, bool chain = false) {
     if (mrhs) {
       for (size_t i = 0; i < mgroups.size(); ++i) {
         BMApply a = mgroups[i].a;
@@ -118,7 +119,8 @@ struct Batch {
       a.coef_off = coef_off;
       a.gate = gate;
       a.step = step;
-      TRY(launch_bapply(prec, g.n, a, s));
+      a.poly_blocks = chain ? 1 : 0;
+      TRY(launch_bapply(chain ? poly_prec : prec, g.n, a, s));
     }
     return COARSE_OK;
   }
@@ -129,10 +131,10 @@ struct Batch {
       *result = xsel;
       return COARSE_OK;
     }
-    TRY(apply_phase(APPLY_POLY_FIRST, xsel, BS_SA, 0, gate, s));
+    TRY(apply_phase(APPLY_POLY_FIRST, xsel, BS_SA, 0, gate, s, true));
     for (int i = 2; i < dd; ++i) {
       const bool even = (i % 2) == 0;
-      TRY(apply_phase(APPLY_POLY, even ? BS_SA : BS_SB, even ? BS_SB : BS_SA, 3 * (i - 1), gate, s));
+      TRY(apply_phase(APPLY_POLY, even ? BS_SA : BS_SB, even ? BS_SB : BS_SA, 3 * (i - 1), gate, s, true));
     }
     *result = BS_ACC;
     return COARSE_OK;
@@ -169,6 +171,7 @@ struct Batch {
       a.coef_off = 0;
       a.gate = BG_NOTDONE;
       a.step = step;
+      a.poly_blocks = 0;
       TRY(launch_bapply64_residual(g.n, a, s));
     }
     return launch_bnorms64(dS, ns, chunk_off, total_chunks, E, 1, s);
@@ -222,6 +225,7 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
 
   // ---- setup per operator: polynomial and recycle space through the single-operator solver
   double setup_ms = 0.0;
+  bool chain_bf16 = false;
   {
     const double ts = now_ms();
     size_t maxN = 0;
@@ -233,7 +237,12 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
       return COARSE_ERR_OOM;
     }
     coarse_solve_params ps = *p;
-    ps.flags = COARSE_ZERO_GUESS;
+    // COARSE_POLY_BF16: FP32 inner solves whose chain phases read BF16 blocks (every operator
+    // must carry them); the setup solves build each recycle space for that same chain
+    bool poly_bf16 = (p->flags & COARSE_POLY_BF16) && prec == COARSE_PREC_FP32;
+    for (int i = 0; i < nops; ++i) poly_bf16 = poly_bf16 && ops[i]->blk[COARSE_PREC_BF16].ptr != nullptr;
+    ps.flags = COARSE_ZERO_GUESS | (poly_bf16 ? COARSE_POLY_BF16 : 0u);
+    chain_bf16 = poly_bf16;
     int rc = COARSE_OK;
     for (int i = 0; i < nops && rc == COARSE_OK; ++i) {
       coarse_op* op = ops[i];
@@ -265,6 +274,7 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   // ---- lockstep batch: descriptors and memory
   Batch B;
   B.prec = prec;
+  B.poly_prec = chain_bf16 ? COARSE_PREC_BF16 : prec;
   B.m = m;
   B.dd = d == 0 ? 0 : std::max(d, 2);
   int ns = 0;
@@ -385,6 +395,7 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
         char* sm = B.mem + off_small[sidx];
         const size_t vb = sizeof(float2) * (size_t)N;
         S.blk = op->blk[prec].ptr;
+        S.blk_poly = op->blk[B.poly_prec].ptr;
         S.blk64 = op->blk[COARSE_PREC_FP64].ptr;
         S.nb = op->nb;
         S.V = op->V;

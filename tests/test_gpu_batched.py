@@ -35,9 +35,10 @@ def problems():
     return out
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-def test_batched_matches_oracle(problems, prec):
-    from paper_2205_09104_gb300 import CoarseOp, solve_batched, solve_params
+@pytest.mark.parametrize("prec,chain_bf16", [(1, False), (2, False), (1, True)])
+def test_batched_matches_oracle(problems, prec, chain_bf16):
+    """chain_bf16: FP32 inner solves whose polynomial-chain phases read BF16 blocks."""
+    from paper_2205_09104_gb300 import COARSE_POLY_BF16, COARSE_ZERO_GUESS, CoarseOp, solve_batched, solve_params
     ops, bs, xs = [], [], []
     for op, mu, B, X, A in problems:
         ops.append(CoarseOp(op.self_blocks.cuda(), op.hop_blocks.cuda(), op.dims, op.nv, mu=mu, precisions=(1, 2),
@@ -45,7 +46,8 @@ def test_batched_matches_oracle(problems, prec):
         bs.append(torch.from_numpy(B).cuda().contiguous())
         xs.append(torch.zeros_like(bs[-1]))
     p = solve_params(m=20, tol=1e-10, precision=prec, poly_degree=4, defl_k=4, recycle_updates=10,
-                     inner_tol=1e-5 if prec == 1 else 1e-2, max_restarts=50, max_ir=40)
+                     inner_tol=1e-5 if prec == 1 else 1e-2, max_restarts=50, max_ir=40,
+                     flags=COARSE_ZERO_GUESS | (COARSE_POLY_BF16 if chain_bf16 else 0))
     infos = solve_batched(ops, bs, xs, p)
     q = 0
     for (op, mu, B, X, A), x in zip(problems, xs):
