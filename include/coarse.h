@@ -167,8 +167,9 @@ int coarse_residual_noalloc(const coarse_op* op, const void* b, const void* x, v
  * q(BF16 blocks) is still one fixed linear operator, so right-preconditioned GMRES and the
  * GCRO-DR recycle space (built for that operator; rebuilt when the choice changes) stay exact;
  * only the preconditioner's quality changes, by the 2^-9 block rounding.  Takes effect for
- * precision COARSE_PREC_FP32 on operators created with BF16 enabled; ignored otherwise and by
- * coarse_solve_batched.  The paper has no counterpart (its coarsest level is single precision). */
+ * precision COARSE_PREC_FP32 on operators created with BF16 enabled (coarse_solve_batched: when
+ * every operator has them); ignored otherwise.  The paper has no counterpart (its coarsest
+ * level is single precision). */
 #define COARSE_POLY_BF16 0x10u
 /* Solve through the odd-even reduced system with block-Jacobi left preconditioning
  * (Sec. 2 and Sec. 3.2): the inner solver (GMRES / polynomial / GCRO-DR) works on
