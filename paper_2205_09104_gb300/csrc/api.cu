@@ -189,11 +189,14 @@ namespace {
 int solve_impl(coarse_op* op, const void* b, void* x, int nrhs, const coarse_solve_params* p,
                coarse_solve_info* info, void* stream, int adjoint) {
   TRY(validate_solve(op, b, x, nrhs, p));
-  const int eo = (p->flags & COARSE_ODD_EVEN) ? 1 : 0;
-  if (eo && (adjoint || p->precision == COARSE_PREC_FP64 || !op->eo_sites)) {
-    set_error("COARSE_ODD_EVEN needs even lattice extents, FP32 or BF16 inner solves and a forward solve");
+  // odd-even reduction: forward solves with FP32/BF16 inner precision; adjoint and FP64 solves
+  // keep the full operator; odd extents cannot be split and are an error
+  int eo = (p->flags & COARSE_ODD_EVEN) ? 1 : 0;
+  if (eo && !op->eo_sites) {
+    set_error("COARSE_ODD_EVEN needs even lattice extents");
     return COARSE_ERR_INVALID_ARG;
   }
+  if (adjoint || p->precision == COARSE_PREC_FP64) eo = 0;
   cudaStream_t s = (cudaStream_t)stream;
   COARSE_CUDA(cudaSetDevice(op->device));
   Solver* sv = get_solver(op, p->precision, adjoint, s, eo);

@@ -82,3 +82,30 @@ def test_gradient_differentiation_workload_sampled():
         ref = -Lm[site, i] * np.conj(Xm[src, j])
         got = gs[site, i, j] if blk == 0 else gh[site, blk - 1, i, j]
         assert abs(got - ref) <= 1e-6 * max(abs(ref), 1e-3 * scale)
+
+
+def test_gradient_with_odd_even_forward():
+    """The forward solve on the odd-even reduced system with the BF16 chain; the backward's
+    adjoint solve falls back to the full operator: gradients as the oracle's."""
+    from paper_2205_09104_gb300 import (COARSE_ODD_EVEN, COARSE_POLY_BF16, COARSE_ZERO_GUESS, CoarseOp, CoarseSolve,
+                                        solve_params)
+    op = make_op((701, 0), (8, 4, 4, 8), 16, m0=-0.4)     # coarse 4x2x2x4 (even extents), n = 32
+    n, V = op.n, op.volume
+    c, b, _ = draws.grad_draws((701, 1), n * V, V, n, 4)
+    S = op.self_blocks.cuda().requires_grad_()
+    H = op.hop_blocks.cuda().requires_grad_()
+    dev = CoarseOp(S.detach(), H.detach(), op.dims, op.nv, precisions=(1, 2))
+    p = solve_params(m=30, tol=1e-12, precision=1, poly_degree=4, defl_k=8, inner_tol=2e-6, max_ir=30,
+                     flags=COARSE_ZERO_GUESS | COARSE_ODD_EVEN | COARSE_POLY_BF16)
+    bt = torch.from_numpy(b).cuda().requires_grad_()
+    x = CoarseSolve.apply(bt, S, H, dev, p)
+    (torch.from_numpy(c).cuda().conj() * x).sum().real.backward()
+    s, h = op.self_blocks.numpy(), op.hop_blocks.numpy()
+    xs = ograd.solve(s, h, op.dims, b)
+    lam = ograd.adjoint_solve(s, h, op.dims, c)
+    rs, rh = ograd.block_gradient(lam, xs, op.dims, n)
+    assert rel(x.detach().cpu().numpy(), xs) <= 1e-9
+    assert rel(bt.grad.cpu().numpy(), lam) <= 1e-6
+    assert rel(S.grad.cpu().numpy(), rs) <= 1e-6
+    assert rel(H.grad.cpu().numpy(), rh) <= 1e-6
+    dev.close()
