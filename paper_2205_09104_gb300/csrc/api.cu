@@ -68,7 +68,9 @@ void free_op(coarse_op* op) {
   if (op->mrhs.ptr) cudaFree(op->mrhs.ptr);
   for (int p = 0; p < 3; ++p) {
     delete op->eo_solver[p];
-    if (op->inv[p].ptr) cudaFree(op->inv[p].ptr);
+    delete op->eo_adj_solver[p];
+    for (int sg = 0; sg < 2; ++sg)
+      if (op->inv[sg][p].ptr) cudaFree(op->inv[sg][p].ptr);
   }
   if (op->eo_sites) cudaFree(op->eo_sites);
   if (op->eo_half) cudaFree(op->eo_half);
@@ -189,14 +191,14 @@ namespace {
 int solve_impl(coarse_op* op, const void* b, void* x, int nrhs, const coarse_solve_params* p,
                coarse_solve_info* info, void* stream, int adjoint) {
   TRY(validate_solve(op, b, x, nrhs, p));
-  // odd-even reduction: forward solves with FP32/BF16 inner precision; adjoint and FP64 solves
-  // keep the full operator; odd extents cannot be split and are an error
+  // odd-even reduction: FP32/BF16 inner precision (FP64 solves keep the full operator); odd
+  // extents cannot be split and are an error
   int eo = (p->flags & COARSE_ODD_EVEN) ? 1 : 0;
   if (eo && !op->eo_sites) {
     set_error("COARSE_ODD_EVEN needs even lattice extents");
     return COARSE_ERR_INVALID_ARG;
   }
-  if (adjoint || p->precision == COARSE_PREC_FP64) eo = 0;
+  if (p->precision == COARSE_PREC_FP64) eo = 0;
   cudaStream_t s = (cudaStream_t)stream;
   COARSE_CUDA(cudaSetDevice(op->device));
   Solver* sv = get_solver(op, p->precision, adjoint, s, eo);
@@ -355,11 +357,12 @@ int coarse_op_update(coarse_op* op, const void* self_blocks, const void* hop_blo
   TRY(check_ptr(self_blocks, "self_blocks"));
   TRY(check_ptr(hop_blocks, "hop_blocks"));
   TRY(ingest(op, self_blocks, hop_blocks, 0, (cudaStream_t)stream));
-  op->inv_ok = 0;
+  op->inv_ok[0] = op->inv_ok[1] = 0;
   for (int p = 0; p < 3; ++p) {
     if (op->solver[p]) op->solver[p]->invalidate();
     if (op->adj_solver[p]) op->adj_solver[p]->invalidate();
     if (op->eo_solver[p]) op->eo_solver[p]->invalidate();
+    if (op->eo_adj_solver[p]) op->eo_adj_solver[p]->invalidate();
   }
   return COARSE_OK;
 }

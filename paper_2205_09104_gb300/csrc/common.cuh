@@ -85,11 +85,11 @@ struct coarse_op {
   // odd-even reduction (all extents even): site lists and inverses of the diagonal blocks
   int* eo_sites = nullptr;          // device [V]: even sites, then odd sites, each in increasing order
   int* eo_half = nullptr;           // device [V]: position of each site in its parity's list
-  coarse::Blocks inv[3];            // per precision: [V][n][n] inverses of A_x + i mu sigma3
-  int inv_ok = 0;                   // inverses valid for the current blocks
-  int inv_sign = 0;                 // ... and for the twisted mass mu * inv_sign
-  void* eo_scratch = nullptr;       // FP32 work vectors of odd-even solves (5 N complex64)
+  coarse::Blocks inv[2][3];         // [mass sign: +mu, -mu][precision]: [V][n][n] inverses of A_x +- i mu sigma3
+  int inv_ok[2] = {0, 0};           // inverses of that sign valid for the current blocks
+  void* eo_scratch = nullptr;       // FP32 work vectors of odd-even solves (3 N complex64)
   coarse::Solver* eo_solver[3] = {nullptr, nullptr, nullptr};
+  coarse::Solver* eo_adj_solver[3] = {nullptr, nullptr, nullptr};  // sigma3 D_c(-mu) sigma3 for mu != 0
   coarse::Solver* solver[3] = {nullptr, nullptr, nullptr};
   coarse::Solver* adj_solver[3] = {nullptr, nullptr, nullptr};  // sigma3 D_c(-mu) sigma3 for mu != 0
   double2* work64 = nullptr;        // 3 FP64 work vectors of V*n: residual, generator scratch, sigma3 temp

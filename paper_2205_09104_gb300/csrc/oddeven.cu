@@ -486,17 +486,18 @@ int eo_prepare(coarse_op* op, double mu_eff, cudaStream_t s) {
               op->dims[2], op->dims[3]);
     return COARSE_ERR_INVALID_ARG;
   }
-  const int sign = mu_eff == op->mu ? 1 : -1;
-  if (op->inv_ok && op->inv_sign == sign) return COARSE_OK;
+  // inverses per mass sign (+mu: D_c, -mu: the adjoint system's D_c(-mu)); mu = 0 has one set
+  const int sg = eo_sign(op, mu_eff);
+  if (op->inv_ok[sg]) return COARSE_OK;
   const int n = op->n;
   const size_t nn = (size_t)op->V * n * n;
   const size_t esz[3] = {sizeof(double2), sizeof(float2), sizeof(cbf16)};
   for (int p = 0; p < 3; ++p) {
-    if (!op->blk[p].ptr || op->inv[p].ptr) continue;
-    op->inv[p].bytes = nn * esz[p];
-    if (cudaMalloc(&op->inv[p].ptr, op->inv[p].bytes) != cudaSuccess) {
+    if (!op->blk[p].ptr || op->inv[sg][p].ptr) continue;
+    op->inv[sg][p].bytes = nn * esz[p];
+    if (cudaMalloc(&op->inv[sg][p].ptr, op->inv[sg][p].bytes) != cudaSuccess) {
       cudaGetLastError();
-      op->inv[p].ptr = nullptr;
+      op->inv[sg][p].ptr = nullptr;
       set_error("odd-even: allocation of the block inverses failed");
       return COARSE_ERR_OOM;
     }
@@ -508,12 +509,12 @@ int eo_prepare(coarse_op* op, double mu_eff, cudaStream_t s) {
     attr = true;
   }
   COARSE_CUDA(cudaMemsetAsync(op->apply_cnt + op->V + 1, 0, sizeof(int), s));
-  k_block_inverse<<<op->V, 256, smem, s>>>((const double2*)op->blk[0].ptr, n, mu_eff, (double2*)op->inv[0].ptr,
+  k_block_inverse<<<op->V, 256, smem, s>>>((const double2*)op->blk[0].ptr, n, mu_eff, (double2*)op->inv[sg][0].ptr,
                                            op->apply_cnt + op->V + 1);
   note_launch();
   COARSE_CUDA(cudaGetLastError());
-  k_inv_convert<<<grid_of(nn), 256, 0, s>>>((const double2*)op->inv[0].ptr, nn, (float2*)op->inv[1].ptr,
-                                             (cbf16*)op->inv[2].ptr);
+  k_inv_convert<<<grid_of(nn), 256, 0, s>>>((const double2*)op->inv[sg][0].ptr, nn, (float2*)op->inv[sg][1].ptr,
+                                             (cbf16*)op->inv[sg][2].ptr);
   note_launch();
   COARSE_CUDA(cudaGetLastError());
   int bad = 0;
@@ -523,8 +524,7 @@ int eo_prepare(coarse_op* op, double mu_eff, cudaStream_t s) {
     set_error("odd-even: a diagonal block A_x + i mu sigma3 is singular");
     return COARSE_ERR_NONFINITE;
   }
-  op->inv_ok = 1;
-  op->inv_sign = sign;
+  op->inv_ok[sg] = 1;
   return COARSE_OK;
 }
 
@@ -639,10 +639,9 @@ int launch_eo_merge(int v64, const void* ev, const void* od, const int* sites, i
 // polynomial-chain epilogue (mode, acc, coef) as the full stencil's.
 int launch_eo_schur(const coarse_op* op, int prec, double mu_eff, const void* x, void* y, void* t, int mode, void* acc,
                     const double2* coef, const int* stop, cudaStream_t s) {
-  (void)mu_eff;
   EoArgs a{};
   a.blocks = op->blk[prec].ptr;
-  a.inv = op->inv[prec].ptr;
+  a.inv = op->inv[eo_sign(op, mu_eff)][prec].ptr;
   a.nb = op->nb;
   a.sites = op->eo_sites;
   a.half = op->eo_half;

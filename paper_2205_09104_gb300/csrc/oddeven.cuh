@@ -24,8 +24,10 @@ struct EoArgs {
   const int* stop;      // optional device flag: return if set
 };
 
+// Index of the inverse set for the twisted mass mu_eff: 0 for +mu (and for mu = 0), 1 for -mu.
+inline int eo_sign(const coarse_op* op, double mu_eff) { return (op->mu != 0.0 && mu_eff != op->mu) ? 1 : 0; }
 // Inverses of the diagonal blocks for the twisted mass mu_eff, in every enabled precision
-// (synchronises s the first time and whenever mu_eff changes sign).
+// (synchronises s the first time for each mass sign).
 int eo_prepare(coarse_op* op, double mu_eff, cudaStream_t s);
 int launch_eo_half(int prec, int n, const EoArgs& a, cudaStream_t s);
 int launch_eo_split(int v64, const void* full, const int* sites, int V, int n, void* ev, void* od, cudaStream_t s);

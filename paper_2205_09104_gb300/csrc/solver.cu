@@ -476,7 +476,8 @@ double now_ms() {
 Solver* get_solver(coarse_op* op, int prec, int adjoint_system, cudaStream_t stream, int odd_even) {
   // With mu = 0, D_c(-mu) = D_c: the adjoint system reuses the forward solver (polynomial, recycle space).
   const bool separate = adjoint_system && op->mu != 0.0;
-  Solver*& slot = odd_even ? op->eo_solver[prec] : (separate ? op->adj_solver[prec] : op->solver[prec]);
+  Solver*& slot = odd_even ? (separate ? op->eo_adj_solver[prec] : op->eo_solver[prec])
+                           : (separate ? op->adj_solver[prec] : op->solver[prec]);
   if (slot == nullptr) {
     slot = new Solver();
     slot->op = op;
@@ -596,7 +597,7 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
       TRY(launch_eo_split(0, eo_full, op->eo_sites, op->V, op->n, eo_re, eo_ro, stream));
       EoArgs a{};
       a.blocks = op->blk[s->prec].ptr;
-      a.inv = op->inv[s->prec].ptr;
+      a.inv = op->inv[eo_sign(op, mu_eff)][s->prec].ptr;
       a.nb = op->nb;
       a.sites = op->eo_sites;
       a.half = op->eo_half;

@@ -94,3 +94,25 @@ def test_odd_extent_rejected():
     with pytest.raises(CoarseError):
         _solve(op, dev, rhs((534, 1), 1, op.volume * op.n)[0], COARSE_ODD_EVEN)
     dev.close()
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.03])
+def test_odd_even_adjoint_solve(ops, mu):
+    """D_c^H lambda = c through the reduced system of sigma3 D_c(-mu) sigma3 (its own inverses and
+    solver for mu != 0), interleaved with forward solves on the same handle."""
+    from paper_2205_09104_gb300 import COARSE_ODD_EVEN, COARSE_ZERO_GUESS, solve_params
+    op = ops[16]
+    dev = _dev(op, mu)
+    N = op.volume * op.n
+    A = ocoarse.assemble(op.self_blocks.numpy(), op.hop_blocks.numpy(), op.dims, mu).tocsc()
+    p = solve_params(m=30, tol=1e-10, precision=1, poly_degree=4, defl_k=8, recycle_updates=5, inner_tol=2e-6,
+                     max_ir=40, flags=COARSE_ZERO_GUESS | COARSE_ODD_EVEN)
+    for i, c in enumerate(rhs((535, 0), 3, N)):
+        lam, info = dev.solve(torch.from_numpy(c).cuda(), params=p, adjoint=True)
+        lam = lam.cpu().numpy()
+        assert info[0]["status"] == 0, info[0]
+        res = np.linalg.norm(c - A.conj().T @ lam) / np.linalg.norm(c)
+        assert res <= 1e-10, res
+        x, info = dev.solve(torch.from_numpy(c).cuda(), params=p)          # forward in between
+        assert np.linalg.norm(c - A @ x.cpu().numpy()) / np.linalg.norm(c) <= 1e-10
+    dev.close()
