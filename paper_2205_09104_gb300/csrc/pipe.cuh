@@ -40,17 +40,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
-// 16-byte asynchronous copy global -> shared through L2 (cp.async.cg), for pieces too small and
-// scattered to be worth a bulk copy each
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-// one arrival on `bar` once every cp.async this thread issued so far has landed (the barrier's
-// expected count must include it)
-__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // Bounded wait that lets the hardware suspend the thread (up to ~20 us per try) instead of
 // re-polling; at most 2^16 tries.  For waits that are usually long (pipeline consumers).
 __device__ __forceinline__ bool mbar_wait_suspend(uint64_t* bar, uint32_t parity) {
