@@ -47,8 +47,12 @@ __device__ void finalize_warp(CycleState* st, const double2* h1, const double2* 
   __shared__ double2 snh[kMaxDense];
   __shared__ double hn2s;
   const int lane = threadIdx.x & 31;
-  if (st->stop) return;  // every lane reads the same flag
-  const int j = st->j, k = st->k, ldh = d.ldh;
+  // all scalar state in one round trip, then everything indexed by j in a second one
+  const int stop0 = st->stop, j = st->j, k = st->k, steps = st->steps, status0 = st->status;
+  const double wn2_raw = st->wnorm2, target = st->target;
+  if (stop0) return;  // every lane reads the same flag
+  const int ldh = d.ldh;
+  const double2 gj = d.g[j];
   double hn2 = 0.0;
   for (int i = lane; i < k; i += 32) {
     const double2 b = add(h1[i], h2[i]);
@@ -68,7 +72,7 @@ __device__ void finalize_warp(CycleState* st, const double2* h1, const double2* 
   for (int off = 16; off > 0; off >>= 1) hn2 += __shfl_xor_sync(0xffffffffu, hn2, off);
   __syncwarp();
   if (lane == 0) {
-    const double wn2 = fmax(st->wnorm2, 0.0);
+    const double wn2 = fmax(wn2_raw, 0.0);
     const double hj1 = sqrt(wn2);
     hn2 += wn2;
     hn2s = hn2;
@@ -86,23 +90,22 @@ __device__ void finalize_warp(CycleState* st, const double2* h1, const double2* 
     d.sn[j] = sg;
     col[j] = r;
     col[j + 1] = make_double2(0.0, 0.0);
-    const double2 gj = d.g[j];
     d.g[j] = scal(gj, c);
     d.g[j + 1] = scal(conjmul(sg, gj), -1.0);
     const double resid = cabs(d.g[j + 1]);
     st->resid = resid;
     st->inv_h = hj1 > 0.0 ? 1.0 / hj1 : 0.0;
-    int stop = 0, status = st->status;
+    int stop = 0, status = status0;
     if (!isfinite(hn2) || !isfinite(resid)) {
       stop = 1;
       status |= ST_NONFINITE;
     } else {
-      if (resid <= st->target) stop = 1;
+      if (resid <= target) stop = 1;
       if (hj1 <= 1e-14 * sqrt(hn2)) {  // invariant Krylov space: the least-squares solution is exact
         stop = 1;
         status |= ST_LUCKY;
       }
-      if (j + 1 >= st->steps) stop = 1;
+      if (j + 1 >= steps) stop = 1;
     }
     st->status = status;
     st->stop = stop;
