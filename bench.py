@@ -454,7 +454,7 @@ def run_schur_only(args):
                       "l2_flush": not args.no_flush, "median_us": round(med * 1e3, 2), "min_us": round(min(ts) * 1e3, 2),
                       "bytes_per_launch": int(nbytes), "achieved_gbs": round(nbytes / (med * 1e-3) / 1e9, 1),
                       "peak_gbs": peak, "frac": round(nbytes / (med * 1e-3) / 1e9 / peak, 4), "peak_source": src,
-                      "launches": len(ts)}), flush=True)
+                      "launches": len(ts), "autotune": cg.autotune_report().splitlines()}), flush=True)
     cop.close()
 
 

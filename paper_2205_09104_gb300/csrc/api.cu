@@ -74,6 +74,7 @@ void free_op(coarse_op* op) {
   }
   if (op->eo_sites) cudaFree(op->eo_sites);
   if (op->eo_half) cudaFree(op->eo_half);
+  if (op->eo_rec) cudaFree(op->eo_rec);
   if (op->eo_scratch) cudaFree(op->eo_scratch);
   if (op->mrhs_x.ptr) cudaFree(op->mrhs_x.ptr);
   if (op->nb) cudaFree(op->nb);
@@ -299,6 +300,7 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
   CREATE_TRY(dmalloc(&op->nb, nb.size() * sizeof(int)));
   // odd-even site lists (every extent even: each hop joins opposite parities)
   std::vector<int> eo_sites, eo_half;
+  std::vector<int4> eo_rec;
   if (L[0] % 2 == 0 && L[1] % 2 == 0 && L[2] % 2 == 0 && L[3] % 2 == 0) {
     eo_sites.resize(op->V);
     eo_half.resize(op->V);
@@ -313,6 +315,15 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
     }
     CREATE_TRY(dmalloc(&op->eo_sites, eo_sites.size() * sizeof(int)));
     CREATE_TRY(dmalloc(&op->eo_half, eo_half.size() * sizeof(int)));
+    eo_rec.resize((size_t)op->V * 4);
+    for (int q = 0; q < op->V; ++q) {
+      const int x = eo_sites[q];
+      for (int mu = 0; mu < 4; ++mu) {
+        const int f = nb[(size_t)x * 8 + mu], b = nb[(size_t)x * 8 + 4 + mu];
+        eo_rec[(size_t)q * 4 + mu] = make_int4(eo_half[f], b, eo_half[b], x);
+      }
+    }
+    CREATE_TRY(dmalloc(&op->eo_rec, eo_rec.size() * sizeof(int4)));
   }
   for (int p = 0; p < 3; ++p) {
     if (!(op->precisions & (1u << p))) continue;
@@ -337,6 +348,8 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
        (cudaMemcpyAsync(op->eo_sites, eo_sites.data(), eo_sites.size() * sizeof(int), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(op->eo_half, eo_half.data(), eo_half.size() * sizeof(int), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(op->eo_rec, eo_rec.data(), eo_rec.size() * sizeof(int4), cudaMemcpyHostToDevice, s) !=
             cudaSuccess)) ||
       cudaMemcpyAsync(op->nb, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(op->red, 0, (2 * 304 + 64) * sizeof(double) + 64, s) != cudaSuccess ||

@@ -85,6 +85,8 @@ struct coarse_op {
   // odd-even reduction (all extents even): site lists and inverses of the diagonal blocks
   int* eo_sites = nullptr;          // device [V]: even sites, then odd sites, each in increasing order
   int* eo_half = nullptr;           // device [V]: position of each site in its parity's list
+  int4* eo_rec = nullptr;           // device [V][4]: for the q-th site x of the (even, odd) list and
+                                    // direction mu, {half index of x+mu, x-mu, half index of x-mu, x}
   coarse::Blocks inv[2][3];         // [mass sign: +mu, -mu][precision]: [V][n][n] inverses of A_x +- i mu sigma3
   int inv_ok[2] = {0, 0};           // inverses of that sign valid for the current blocks
   void* eo_scratch = nullptr;       // FP32 work vectors of odd-even solves (3 N complex64)

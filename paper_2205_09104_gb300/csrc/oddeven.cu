@@ -18,6 +18,7 @@
 #include "apply_core.cuh"
 #include "common.cuh"
 #include "oddeven.cuh"
+#include "pipe.cuh"
 #include "tune.cuh"
 
 namespace coarse {
@@ -108,26 +109,90 @@ __global__ void k_inv_convert(const double2* __restrict__ in, size_t total, floa
 }
 
 // ------------------------------------------------------------------------- the half apply
+// Block rows from shared memory (the prefetched inverse block).
+template <class AC, class BT> struct RowSh;
+template <> struct RowSh<double2, double2> {
+  template <int CPL> __device__ __forceinline__ static void row(const double2* p, double2 (&e)[CPL]) {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) e[c] = p[c];
+  }
+};
+template <> struct RowSh<float2, float2> {
+  template <int CPL> __device__ __forceinline__ static void row(const float2* p, float2 (&e)[CPL]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int c = 0; c < CPL / 2; ++c) {
+      const float4 v = q[c];
+      e[2 * c] = make_float2(v.x, v.y);
+      e[2 * c + 1] = make_float2(v.z, v.w);
+    }
+  }
+};
+template <> struct RowSh<float2, cbf16> {
+  template <int CPL> __device__ __forceinline__ static void row(const cbf16* p, float2 (&e)[CPL]) {
+    const uint2* q = reinterpret_cast<const uint2*>(p);
+#pragma unroll
+    for (int c = 0; c < CPL / 2; ++c) {
+      const uint2 v = q[c];
+      e[2 * c] = bf2f(v.x);
+      e[2 * c + 1] = bf2f(v.y);
+    }
+  }
+};
+
 // One CTA of W warps (W = 4 or 2) per output site x: warp w computes, for its directions
 // mu = w, w + W, ..., the forward hop F_{x,mu} v_{x+mu} (row sums) and the backward hop
 // sigma3 F_{x-mu,mu}^H sigma3 v_{x-mu} (column sums) into its own slot; h is the sum of the W
 // slots in fixed order (deterministic); the inverse block's rows are split over the warps; the
-// epilogue runs over the CTA, coalesced.
-template <int N, class BT, class VT, class AC, int W, bool UNROLL = false>
-__global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
+// epilogue runs over the CTA, coalesced.  The site's neighbour record (EoArgs::rec) gives every
+// index in one round trip.  PF: thread 0 starts bulk copies of the inverse block and of the
+// epilogue's vectors (z, base, acc) into shared memory before the hops, so that nothing after
+// the hop sums waits on DRAM; their mbarrier wait is bounded (on expiry: *err raised, the
+// copies drained with a second bounded wait, return).  PF needs 16-byte aligned vectors
+// (checked by the launcher).
+//
+// Occupancy: with 2 warps per site and n = 32 in FP32/BF16, 72 registers let 14 CTAs share an SM,
+// so that the 2048 sites of one parity of an 8^4 lattice fit in one wave on 152 SMs; the
+// prefetching variants are held to that.
+template <int N, class AC, int W, bool PF>
+constexpr int eo_min_blocks() {
+  return (PF && W == 2 && N == 32 && sizeof(decltype(AC{}.x)) == 4) ? 14 : 0;
+}
+template <int N, class BT, class VT, class AC, int W, bool UNROLL = false, bool PF = false>
+__global__ void __launch_bounds__(32 * W, eo_min_blocks<N, AC, W, PF>()) k_eo_half(EoArgs a) {
   constexpr int CPL = N / 8, KR = N / 4, NV = N / 2, KW = KR / W;  // KW row quads per warp
   constexpr size_t BSZ = (size_t)N * N;
   using AT = decltype(AC{}.x);
   __shared__ AC hpart[W][N];
   __shared__ AC us[N];
+  __shared__ __align__(16) BT sinv[PF ? N * N : 1];
+  __shared__ __align__(16) VT svec[PF ? 3 * N : 1];  // z, base, acc of this site
+  __shared__ __align__(8) uint64_t sbar;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 3, t = lane & 7;
-  const int k = blockIdx.x;
-  if (k >= a.V / 2) return;  // CTA-uniform
+  const int k = blockIdx.x, nh = a.V / 2;
+  if (k >= nh) return;  // CTA-uniform
+  const int4* rp = a.rec + ((size_t)a.out_par * nh + k) * 4;
+  int4 rc[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) rc[mu] = __ldg(rp + mu);
   if (a.stop && *a.stop) return;
-  const int x = __ldg(a.sites + a.out_par * (a.V / 2) + k);
+  const int x = rc[0].w;
   const BT* B = static_cast<const BT*>(a.blocks);
   const VT* v = static_cast<const VT*>(a.v);
+  const VT* z = static_cast<const VT*>(a.z);
+  const VT* base = static_cast<const VT*>(a.base);
+  const bool acc_in = a.mode != APPLY_PLAIN && a.mode != APPLY_POLY_FIRST;
+  if (PF && threadIdx.x == 0) {
+    constexpr uint32_t ib = (uint32_t)(BSZ * sizeof(BT)), vb = (uint32_t)(N * sizeof(VT));
+    mbar_init(&sbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&sbar, ib + (z ? vb : 0u) + (base ? vb : 0u) + (acc_in ? vb : 0u));
+    bulk_g2s(sinv, static_cast<const BT*>(a.inv) + (size_t)x * BSZ, ib, &sbar);
+    if (z) bulk_g2s(svec, z + (size_t)k * N, vb, &sbar);
+    if (base) bulk_g2s(svec + N, base + (size_t)k * N, vb, &sbar);
+    if (acc_in) bulk_g2s(svec + 2 * N, static_cast<const VT*>(a.acc) + (size_t)k * N, vb, &sbar);
+  }
   const AT st = (t * CPL < NV) ? AT(1) : AT(-1);  // sigma3 of this lane's columns
 
   AC yf[KR], yb[CPL];
@@ -140,9 +205,8 @@ __global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
 #pragma unroll (UNROLL ? 4 : 1)
     for (int mu = wid; mu < 4; mu += W) {
       // forward hop: row sums of F_{x,mu} v_{x+mu}; backward: column sums of conj(F_{x-mu,mu}) (sigma3 v)
-      const int fsrc = __ldg(a.half + __ldg(a.nb + x * 8 + mu));
-      const int nbx = __ldg(a.nb + x * 8 + 4 + mu);
-      const int bsrc = __ldg(a.half + nbx);
+      const int4 q = mu == 0 ? rc[0] : mu == 1 ? rc[1] : mu == 2 ? rc[2] : rc[3];
+      const int fsrc = q.x, nbx = q.y, bsrc = q.z;
       AC w[CPL], xr[KR];
       load_vec<VT, AC, CPL>(v + (size_t)fsrc * N + t * CPL, w);
 #pragma unroll
@@ -189,10 +253,18 @@ __global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
   if (g == 0)
 #pragma unroll
     for (int c = 0; c < CPL; ++c) hp[t * CPL + c] = cadd(hp[t * CPL + c], cscale(yb[c], st));
-  __syncthreads();
+  if constexpr (PF) {
+    // CTA-uniform outcome of the bounded wait for the prefetched inverse and vectors
+    if (!__syncthreads_and(mbar_wait(&sbar, 0))) {
+      if (threadIdx.x == 0) atomicExch(a.err, 1);
+      mbar_wait(&sbar, 0);  // drain (bounded)
+      return;
+    }
+  } else {
+    __syncthreads();
+  }
   // g = z - h (or h), h = sum of the 4 direction slots: this lane's column chunk
   AC gi[CPL];
-  const VT* z = static_cast<const VT*>(a.z);
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
     const int j = t * CPL + c;
@@ -200,7 +272,7 @@ __global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
 #pragma unroll
     for (int q = 1; q < W; ++q) hv = cadd(hv, hpart[q][j]);
     if (z) {
-      const VT zv = z[(size_t)k * N + j];
+      const VT zv = PF ? svec[j] : z[(size_t)k * N + j];
       gi[c] = AC{AT(zv.x) - hv.x, AT(zv.y) - hv.y};
     } else {
       gi[c] = hv;
@@ -211,11 +283,12 @@ __global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
     AC uf[KW];
 #pragma unroll
     for (int q = 0; q < KW; ++q) uf[q] = AC{0, 0};
-    const BT* blk = static_cast<const BT*>(a.inv) + (size_t)x * BSZ + g * N + t * CPL;
 #pragma unroll
     for (int q = 0; q < KW; ++q) {
       AC e[CPL];
-      LoadS<AC, BT>::template row<CPL>(blk + (size_t)(wid * KW + q) * 4 * N, e);
+      const size_t off = (size_t)(wid * KW + q) * 4 * N + g * N + t * CPL;
+      if constexpr (PF) RowSh<AC, BT>::template row<CPL>(sinv + off, e);
+      else LoadS<AC, BT>::template row<CPL>(static_cast<const BT*>(a.inv) + (size_t)x * BSZ + off, e);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) cfma(uf[q], e[c], gi[c]);
     }
@@ -232,7 +305,6 @@ __global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
   }
   __syncthreads();
   // epilogue over the CTA, coalesced: y = u or base - u, then the chain step with x = base
-  const VT* base = static_cast<const VT*>(a.base);
   VT* y = static_cast<VT*>(a.y);
   const double2 c0d = a.mode != APPLY_PLAIN ? a.coef[0] : make_double2(0.0, 0.0);
   const double2 c1d = a.mode != APPLY_PLAIN ? a.coef[1] : make_double2(0.0, 0.0);
@@ -243,7 +315,7 @@ __global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
     AC r = us[e];
     AC xs{0, 0};
     if (base) {
-      const VT bv = base[idx];
+      const VT bv = PF ? svec[N + e] : base[idx];
       xs = AC{AT(bv.x), AT(bv.y)};
       r = csub(xs, r);
     }
@@ -259,7 +331,7 @@ __global__ void __launch_bounds__(32 * W) k_eo_half(EoArgs a) {
       if (a.mode == APPLY_POLY_FIRST) {
         ac = cmul(c2, xs);
       } else {
-        const VT av = *accp;
+        const VT av = PF ? svec[2 * N + e] : *accp;
         ac = AC{AT(av.x), AT(av.y)};
       }
       const AC sp = csub(xs, cmul(c0, r));
@@ -289,7 +361,8 @@ __global__ void __launch_bounds__(128) k_eo_half_w(EoArgs a) {
   const int k = blockIdx.x * 4 + warp;
   if (k >= half) return;  // warp-uniform
   if (a.stop && *a.stop) return;
-  const int x = __ldg(a.sites + a.out_par * half + k);
+  const int4* rp = a.rec + ((size_t)a.out_par * half + k) * 4;
+  const int x = __ldg(rp).w;
   const BT* B = static_cast<const BT*>(a.blocks);
   const VT* v = static_cast<const VT*>(a.v);
   AC* s = sh[warp];
@@ -305,7 +378,7 @@ __global__ void __launch_bounds__(128) k_eo_half_w(EoArgs a) {
     for (int mu = 0; mu < 4; ++mu) {
       // forward hop: row sums of F_{x,mu} v_{x+mu}
       {
-        const int src = __ldg(a.half + __ldg(a.nb + x * 8 + mu));
+        const int src = __ldg(rp + mu).x;
         AC w[CPL];
         load_vec<VT, AC, CPL>(v + (size_t)src * N + t * CPL, w);
         const BT* blk = B + ((size_t)x * 5 + 1 + mu) * BSZ + g * N + t * CPL;
@@ -319,8 +392,8 @@ __global__ void __launch_bounds__(128) k_eo_half_w(EoArgs a) {
       }
       // backward hop: column sums of conj(F_{x-mu,mu}) (sigma3 v_{x-mu})
       {
-        const int nbx = __ldg(a.nb + x * 8 + 4 + mu);
-        const int src = __ldg(a.half + nbx);
+        const int4 q = __ldg(rp + mu);
+        const int nbx = q.y, src = q.z;
         AC xr[KR];
 #pragma unroll
         for (int r = 0; r < KR; ++r) {
@@ -447,6 +520,308 @@ __global__ void __launch_bounds__(128) k_eo_half_w(EoArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ the streamed half apply
+// Persistent variant: one CTA of 8 warps per SM walks the sites k = blockIdx.x + i * gridDim.x of
+// the output parity.  Warp w owns one hop block of every site (w < 4: F_{x,mu}, w >= 4:
+// F_{x-mu,mu} with mu = w & 3) and feeds its own shared-memory ring: lane 0 bulk-copies the block
+// and the input vector it multiplies S sites ahead, completing on the stage's mbarrier.  Thread 0
+// feeds a three-stage ring with the inverse block and the epilogue's vectors (z, base, acc).  The
+// bytes in flight per SM are then set by the rings (8 S blocks), not by registers, which keeps HBM
+// busy with few warps.  Per site: each warp reduces its block against its vector into its slot of
+// hpart; barrier; g = z - sum of the 8 slots (fixed order); u = B_x^{-1} g with the inverse's row
+// quads split over the warps; barrier; the epilogue as in k_eo_half.  A stage is refilled only
+// after its readers are done (every value read from it has been consumed): a hop stage by its own
+// warp after __syncwarp, an inverse stage one site later, after the next CTA barrier.  (A proxy
+// fence there would make the refilling thread wait for its own earlier global stores, a round
+// trip per site on the critical path.)  Every wait is bounded; an
+// expired wait ends the loop for the whole CTA (the barriers are __syncthreads_or), raises *err
+// and drains the copies still in flight with bounded waits.  Needs v and 16-byte aligned vectors.
+constexpr int kEoRingWarps = 8, kEoInvStages = 3, kEoRingMaxS = 6;
+
+// Block-row chunk from shared memory.  For 32-byte chunks (FP32, n = 32) lanes 4..7 of each
+// quarter warp take the two 16-byte halves in the opposite order, so that the 8 lanes of a
+// 128-bit load phase hit distinct bank groups.
+template <class AC, class BT, int CPL>
+__device__ __forceinline__ void ring_row(const BT* p, int t, AC (&e)[CPL]) {
+  if constexpr (sizeof(BT) == 8 && sizeof(AC) == 8 && CPL == 4) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const int h = (t >> 2) & 1;
+    const float4 a = q[h], b = q[h ^ 1];
+    const float4 lo = h ? b : a, hi = h ? a : b;
+    e[0] = make_float2(lo.x, lo.y);
+    e[1] = make_float2(lo.z, lo.w);
+    e[2] = make_float2(hi.x, hi.y);
+    e[3] = make_float2(hi.z, hi.w);
+  } else if constexpr (sizeof(BT) == 4 && (CPL * 4) % 16 == 0) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int c = 0; c < CPL / 4; ++c) {
+      const uint4 v = q[c];
+      e[4 * c] = bf2f(v.x);
+      e[4 * c + 1] = bf2f(v.y);
+      e[4 * c + 2] = bf2f(v.z);
+      e[4 * c + 3] = bf2f(v.w);
+    }
+  } else {
+    RowSh<AC, BT>::template row<CPL>(p, e);
+  }
+}
+
+template <int N, class BT, class VT, class AC>
+__global__ void __launch_bounds__(32 * kEoRingWarps, 1) k_eo_ring(EoArgs a, int S) {
+  constexpr int CPL = N / 8, KR = N / 4, NV = N / 2, NI = kEoInvStages;
+  constexpr size_t BSZ = (size_t)N * N;
+  constexpr uint32_t BB = (uint32_t)(BSZ * sizeof(BT)), VB = (uint32_t)(N * sizeof(VT));
+  constexpr uint32_t HS = BB + VB, IS = BB + 3 * VB;  // hop and inverse stage bytes
+  using AT = decltype(AC{}.x);
+  extern __shared__ __align__(128) unsigned char ring_smem[];
+  __shared__ AC hpart[kEoRingWarps][N];
+  __shared__ AC us[N];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 3, t = lane & 7;
+  const int mu = wid & 3;
+  const bool bwd = wid >= 4;
+  const int nh = a.V / 2, G = gridDim.x, k0 = blockIdx.x;
+  if (k0 >= nh) return;  // CTA-uniform
+  if (a.stop && *a.stop) return;
+  unsigned char* hop = ring_smem + (size_t)wid * S * HS;
+  unsigned char* invs = ring_smem + (size_t)kEoRingWarps * S * HS;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(invs + (size_t)NI * IS);
+  uint64_t* hb = bars + wid * S;               // this warp's hop stages
+  uint64_t* ib = bars + kEoRingWarps * S;      // inverse stages
+  const int cnt = (nh - k0 + G - 1) / G;       // sites of this CTA
+  const int4* R = a.rec + (size_t)a.out_par * nh * 4;
+  const BT* B = static_cast<const BT*>(a.blocks);
+  const BT* INV = static_cast<const BT*>(a.inv);
+  const VT* v = static_cast<const VT*>(a.v);
+  const VT* z = static_cast<const VT*>(a.z);
+  const VT* base = static_cast<const VT*>(a.base);
+  VT* acc = static_cast<VT*>(a.acc);
+  const bool acc_in = a.mode != APPLY_PLAIN && a.mode != APPLY_POLY_FIRST;
+  const uint32_t inv_tx = BB + (z ? VB : 0u) + (base ? VB : 0u) + (acc_in ? VB : 0u);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kEoRingWarps * S + NI; ++i) mbar_init(bars + i, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // ring feeders: site i of this CTA into stage i % S (hop) or i % NI (inverse)
+  auto issue_hop = [&](int i, int4 q) {
+    uint64_t* bar = hb + i % S;
+    unsigned char* st = hop + (size_t)(i % S) * HS;
+    mbar_expect_tx(bar, HS);
+    const size_t owner = bwd ? (size_t)q.y : (size_t)q.w;
+    bulk_g2s(st, B + (owner * 5 + 1 + mu) * BSZ, BB, bar);
+    bulk_g2s(st + BB, v + (size_t)(bwd ? q.z : q.x) * N, VB, bar);
+  };
+  auto issue_inv = [&](int i, int x) {
+    const size_t k = (size_t)k0 + (size_t)i * G;
+    uint64_t* bar = ib + i % NI;
+    unsigned char* st = invs + (size_t)(i % NI) * IS;
+    mbar_expect_tx(bar, inv_tx);
+    bulk_g2s(st, INV + (size_t)x * BSZ, BB, bar);
+    if (z) bulk_g2s(st + BB, z + k * N, VB, bar);
+    if (base) bulk_g2s(st + BB + VB, base + k * N, VB, bar);
+    if (acc_in) bulk_g2s(st + BB + 2 * VB, acc + k * N, VB, bar);
+  };
+  int hop_issued = 0, inv_issued = 0;
+  if (lane == 0) {
+    int4 q[kEoRingMaxS];
+#pragma unroll
+    for (int i = 0; i < kEoRingMaxS; ++i)
+      if (i < S && i < cnt) q[i] = __ldg(R + ((size_t)k0 + (size_t)i * G) * 4 + mu);
+#pragma unroll
+    for (int i = 0; i < kEoRingMaxS; ++i)
+      if (i < S && i < cnt) issue_hop(i, q[i]);
+    hop_issued = min(S, cnt);
+  }
+  if (threadIdx.x == 0) {
+    int xs[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+      if (i < cnt) xs[i] = __ldg(R + ((size_t)k0 + (size_t)i * G) * 4).w;
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+      if (i < cnt) issue_inv(i, xs[i]);
+    inv_issued = min(NI, cnt);
+  }
+  const AT st = (t * CPL < NV) ? AT(1) : AT(-1);  // sigma3 of this lane's columns
+  const double2 c0d = a.mode != APPLY_PLAIN ? a.coef[0] : make_double2(0.0, 0.0);
+  const double2 c1d = a.mode != APPLY_PLAIN ? a.coef[1] : make_double2(0.0, 0.0);
+  const double2 c2d = a.mode == APPLY_POLY_FIRST ? a.coef[2] : make_double2(0.0, 0.0);
+  const AC c0{AT(c0d.x), AT(c0d.y)}, c1{AT(c1d.x), AT(c1d.y)}, c2{AT(c2d.x), AT(c2d.y)};
+  VT* y = static_cast<VT*>(a.y);
+  bool failed = false;
+  int i = 0;
+  // records for the refills, loaded one iteration before their use: iteration i refills the hop
+  // stage with site i + S and the inverse stage with site i - 1 + NI
+  int4 qn = make_int4(0, 0, 0, 0);
+  int xn = 0;
+  if (lane == 0 && S < cnt) qn = __ldg(R + ((size_t)k0 + (size_t)S * G) * 4 + mu);
+  for (; i < cnt; ++i) {
+    const size_t k = (size_t)k0 + (size_t)i * G;
+    int4 qnn = make_int4(0, 0, 0, 0);
+    if (lane == 0 && i + 1 + S < cnt) qnn = __ldg(R + ((size_t)k0 + (size_t)(i + 1 + S) * G) * 4 + mu);
+    int xnn = 0;
+    if (threadIdx.x == 0 && i + NI < cnt) xnn = __ldg(R + ((size_t)k0 + (size_t)(i + NI) * G) * 4).w;
+    // warp-uniform outcome (the shuffles below need the whole warp)
+    bool ok = __all_sync(0xffffffffu, mbar_wait(hb + i % S, (uint32_t)((i / S) & 1)));
+    if (ok) {
+      const unsigned char* sp = hop + (size_t)(i % S) * HS;
+      const BT* blk = reinterpret_cast<const BT*>(sp) + g * N + t * CPL;
+      const VT* vec = reinterpret_cast<const VT*>(sp + BB);
+      if (!bwd) {
+        // row sums of F_{x,mu} v_{x+mu}
+        AC w[CPL], yf[KR];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const VT vv = vec[t * CPL + c];
+          w[c] = AC{AT(vv.x), AT(vv.y)};
+        }
+#pragma unroll
+        for (int r = 0; r < KR; ++r) {
+          AC e[CPL];
+          ring_row<AC, BT, CPL>(blk + (size_t)r * 4 * N, t, e);
+          yf[r] = AC{0, 0};
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) cfma(yf[r], e[c], w[c]);
+        }
+#pragma unroll
+        for (int r = 0; r < KR; ++r)
+#pragma unroll
+          for (int off = 1; off < 8; off <<= 1) {
+            yf[r].x += __shfl_xor_sync(0xffffffffu, yf[r].x, off);
+            yf[r].y += __shfl_xor_sync(0xffffffffu, yf[r].y, off);
+          }
+        if (t == 0)
+#pragma unroll
+          for (int r = 0; r < KR; ++r) hpart[wid][4 * r + g] = yf[r];
+      } else {
+        // column sums of conj(F_{x-mu,mu}) (sigma3 v_{x-mu}), then sigma3 on the result
+        AC yb[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) yb[c] = AC{0, 0};
+#pragma unroll
+        for (int r = 0; r < KR; ++r) {
+          const VT vv = vec[4 * r + g];
+          const AT sk = (4 * r + g < NV) ? AT(1) : AT(-1);
+          const AC xr{sk * AT(vv.x), sk * AT(vv.y)};
+          AC f[CPL];
+          ring_row<AC, BT, CPL>(blk + (size_t)r * 4 * N, t, f);
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) cfma_conj(yb[c], f[c], xr);
+        }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+          for (int off = 8; off < 32; off <<= 1) {
+            yb[c].x += __shfl_xor_sync(0xffffffffu, yb[c].x, off);
+            yb[c].y += __shfl_xor_sync(0xffffffffu, yb[c].y, off);
+          }
+        if (g == 0)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) hpart[wid][t * CPL + c] = cscale(yb[c], st);
+      }
+    }
+    // the warp's reads of this stage are complete (their values are in hpart): refill it
+    __syncwarp();
+    if (ok && lane == 0 && i + S < cnt) {
+      issue_hop(i + S, qn);
+      ++hop_issued;
+    }
+    qn = qnn;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    // every thread is past the epilogue of site i - 1: its inverse stage takes site i - 1 + NI
+    if (threadIdx.x == 0 && i >= 1 && i - 1 + NI < cnt) {
+      issue_inv(i - 1 + NI, xn);
+      ++inv_issued;
+    }
+    xn = xnn;
+    ok = __all_sync(0xffffffffu, mbar_wait(ib + i % NI, (uint32_t)((i / NI) & 1)));
+    const unsigned char* ip = invs + (size_t)(i % NI) * IS;
+    const VT* sv = reinterpret_cast<const VT*>(ip + BB);  // z, base, acc
+    if (ok) {
+      AC gi[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int j = t * CPL + c;
+        AC hv = hpart[0][j];
+#pragma unroll
+        for (int q = 1; q < kEoRingWarps; ++q) hv = cadd(hv, hpart[q][j]);
+        if (z) {
+          const VT zv = sv[j];
+          gi[c] = AC{AT(zv.x) - hv.x, AT(zv.y) - hv.y};
+        } else {
+          gi[c] = hv;
+        }
+      }
+      const BT* iblk = reinterpret_cast<const BT*>(ip) + g * N + t * CPL;
+      for (int q = wid; q < KR; q += kEoRingWarps) {
+        AC e[CPL];
+        ring_row<AC, BT, CPL>(iblk + (size_t)q * 4 * N, t, e);
+        AC uf{0, 0};
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) cfma(uf, e[c], gi[c]);
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+          uf.x += __shfl_xor_sync(0xffffffffu, uf.x, off);
+          uf.y += __shfl_xor_sync(0xffffffffu, uf.y, off);
+        }
+        if (t == 0) us[4 * q + g] = uf;
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    for (int e = threadIdx.x; e < N; e += blockDim.x) {
+      const size_t idx = k * N + e;
+      AC r = us[e];
+      AC xs{0, 0};
+      if (base) {
+        const VT bv = sv[N + e];
+        xs = AC{AT(bv.x), AT(bv.y)};
+        r = csub(xs, r);
+      }
+      if (a.mode == APPLY_PLAIN) {
+        VT o;
+        o.x = r.x;
+        o.y = r.y;
+        y[idx] = o;
+      } else {
+        // chain step on S: s' = x - c0 (S x) ; acc = acc + c1 s'  (first: acc = c2 x + c1 s')
+        AC ac;
+        if (a.mode == APPLY_POLY_FIRST) {
+          ac = cmul(c2, xs);
+        } else {
+          const VT av = sv[2 * N + e];
+          ac = AC{AT(av.x), AT(av.y)};
+        }
+        const AC spv = csub(xs, cmul(c0, r));
+        ac = cadd(ac, cmul(c1, spv));
+        VT o;
+        o.x = spv.x;
+        o.y = spv.y;
+        y[idx] = o;
+        VT ao;
+        ao.x = ac.x;
+        ao.y = ac.y;
+        acc[idx] = ao;
+      }
+    }
+  }
+  if (failed) {
+    // drain: each stage holds at most one outstanding copy group, the last S (NI) issued
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    if (lane == 0)
+      for (int j = max(i, hop_issued - S); j < hop_issued; ++j) mbar_wait(hb + j % S, (uint32_t)((j / S) & 1));
+    if (threadIdx.x == 0)
+      for (int j = max(i, inv_issued - NI); j < inv_issued; ++j) mbar_wait(ib + j % NI, (uint32_t)((j / NI) & 1));
+  }
+}
+
 // full vector <-> (even, odd) compressed halves
 template <class VT>
 __global__ void k_eo_split(const VT* __restrict__ full, const int* __restrict__ sites, int V, int n, VT* ev, VT* od) {
@@ -530,14 +905,71 @@ int eo_prepare(coarse_op* op, double mu_eff, cudaStream_t s) {
 
 namespace {
 
+// The streamed layout: S hop stages per warp, as many as fit next to the inverse ring (at most
+// kEoRingMaxS); one CTA per SM.  INVALID_ARG if not even one stage fits.
+template <int N, class BT, class VT, class AC>
+int launch_eo_ring_n(const EoArgs& a, cudaStream_t s) {
+  constexpr size_t HS = (size_t)N * N * sizeof(BT) + N * sizeof(VT);
+  constexpr size_t IS = (size_t)N * N * sizeof(BT) + 3 * N * sizeof(VT);
+  static int S = -1;
+  static size_t dyn = 0;
+  if (S < 0) {
+    int dev = 0, optin = 0;
+    COARSE_CUDA(cudaGetDevice(&dev));
+    COARSE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    COARSE_CUDA(cudaFuncGetAttributes(&fa, k_eo_ring<N, BT, VT, AC>));
+    // the rings and mbarriers, next to the static shared memory and the dynamic part's alignment
+    int sv = kEoRingMaxS;
+    for (; sv >= 1; --sv) {
+      dyn = (size_t)kEoRingWarps * sv * HS + kEoInvStages * IS + 8 * (size_t)(kEoInvStages + kEoRingWarps * sv);
+      if (dyn + fa.sharedSizeBytes + 128 <= (size_t)optin) break;
+    }
+    if (sv >= 1)
+      COARSE_CUDA(cudaFuncSetAttribute(k_eo_ring<N, BT, VT, AC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)dyn));
+    S = std::max(sv, 0);
+  }
+  if (S < 1) {
+    set_error("odd-even: the streamed layout does not fit in shared memory for n = %d", N);
+    return COARSE_ERR_INVALID_ARG;
+  }
+  const int grid = std::min(a.V / 2, sm_count());
+  k_eo_ring<N, BT, VT, AC><<<grid, 32 * kEoRingWarps, dyn, s>>>(a, S);
+  return COARSE_OK;
+}
+
 template <class BT, class VT, class AC>
 int launch_eo_variant(int variant, int n, const EoArgs& a, cudaStream_t s) {
   const int half = a.V / 2;
+  // the prefetching and streamed variants copy vectors with bulk copies: 16-byte aligned only
+  const uintptr_t al = (uintptr_t)a.z | (uintptr_t)a.base | (uintptr_t)a.acc | (uintptr_t)a.inv;
+  if (variant == 6) {
+    if constexpr (sizeof(decltype(AC{}.x)) == 4) {
+      if (a.v && !((al | (uintptr_t)a.v) & 15)) {
+        int rc = COARSE_ERR_INVALID_ARG;
+        switch (n) {
+          case 16: rc = launch_eo_ring_n<16, BT, VT, AC>(a, s); break;
+          case 32: rc = launch_eo_ring_n<32, BT, VT, AC>(a, s); break;
+          case 48: rc = launch_eo_ring_n<48, BT, VT, AC>(a, s); break;
+          default: set_error("odd-even: unsupported n = %d", n);
+        }
+        if (rc != COARSE_OK) return rc;
+        note_launch();
+        COARSE_CUDA(cudaGetLastError());
+        return COARSE_OK;
+      }
+    }
+    variant = 4;  // FP64 blocks, no hop input (the right-hand side pass) or unaligned vectors
+  }
+  if (variant >= 4 && (al & 15)) variant -= 2;
 #define EO_LAUNCH(NN)                                                                           \
   case NN:                                                                                      \
     if (variant == 1) k_eo_half_w<NN, BT, VT, AC><<<(half + 3) / 4, 128, 0, s>>>(a);             \
     else if (variant == 2) k_eo_half<NN, BT, VT, AC, 2><<<half, 64, 0, s>>>(a);                  \
     else if (variant == 3) k_eo_half<NN, BT, VT, AC, 2, true><<<half, 64, 0, s>>>(a);            \
+    else if (variant == 4) k_eo_half<NN, BT, VT, AC, 2, false, true><<<half, 64, 0, s>>>(a);     \
+    else if (variant == 5) k_eo_half<NN, BT, VT, AC, 2, true, true><<<half, 64, 0, s>>>(a);      \
     else k_eo_half<NN, BT, VT, AC, 4><<<half, 128, 0, s>>>(a);                                   \
     break;
   switch (n) {
@@ -554,8 +986,9 @@ int launch_eo_variant(int variant, int n, const EoArgs& a, cudaStream_t s) {
 
 // The autotuner picks, per (precision, n, lattice-size bucket), between one CTA of 4 warps per
 // site (candidate 0), one warp per site (candidate 1) and one CTA of 2 warps per site with the
-// direction loop rolled (candidate 2) or unrolled (candidate 3); candidates run in plain mode into
-// a scratch output.
+// direction loop rolled (candidates 2, 4) or unrolled (3, 5), the last two with the inverse block
+// and the epilogue vectors prefetched into shared memory, and (FP32 / BF16 blocks) the streamed
+// persistent layout (6); candidates run in plain mode into a scratch output.
 template <class BT, class VT, class AC>
 int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
   static int choice[3][32];
@@ -574,13 +1007,20 @@ int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
     char key[64];
     snprintf(key, sizeof(key), "eo/p%d/n%d/v%d", prec, n, vb);
     void* scratch = nullptr;
+    const size_t hv = (size_t)(a.V / 2) * n;
     auto run = [&](const TuneChoice& c) -> int {
-      if (!scratch && cudaMalloc(&scratch, sizeof(VT) * (size_t)(a.V / 2) * n) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("odd-even: autotuner scratch allocation failed");
-        return COARSE_ERR_OOM;
+      if (!scratch) {
+        if (cudaMalloc(&scratch, 2 * sizeof(VT) * hv) != cudaSuccess) {
+          cudaGetLastError();
+          scratch = nullptr;
+          set_error("odd-even: autotuner scratch allocation failed");
+          return COARSE_ERR_OOM;
+        }
+        COARSE_CUDA(cudaMemsetAsync(scratch, 0, 2 * sizeof(VT) * hv, s));
       }
       EoArgs t = a;
+      // candidates are always timed with the hops (a pass without them is not representative)
+      if (!t.v) t.v = static_cast<VT*>(scratch) + hv;
       t.mode = APPLY_PLAIN;
       t.y = scratch;
       t.acc = nullptr;
@@ -591,8 +1031,10 @@ int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     TuneChoice c;
-    const int rc = tune_pick(key, {TuneChoice{0, 0, 0}, TuneChoice{1, 0, 0}, TuneChoice{2, 0, 0}, TuneChoice{3, 0, 0}},
-                             run, s, &c);
+    std::vector<TuneChoice> cands;
+    for (int v = 0; v <= 6; ++v)
+      if (v < 6 || sizeof(decltype(AC{}.x)) == 4) cands.push_back(TuneChoice{v, 0, 0});
+    const int rc = tune_pick(key, cands, run, s, &c);
     if (scratch) {
       cudaStreamSynchronize(s);
       cudaFree(scratch);
@@ -642,9 +1084,8 @@ int launch_eo_schur(const coarse_op* op, int prec, double mu_eff, const void* x,
   EoArgs a{};
   a.blocks = op->blk[prec].ptr;
   a.inv = op->inv[eo_sign(op, mu_eff)][prec].ptr;
-  a.nb = op->nb;
-  a.sites = op->eo_sites;
-  a.half = op->eo_half;
+  a.rec = op->eo_rec;
+  a.err = op->apply_cnt + op->V;
   a.V = op->V;
   a.stop = stop;
   // t_o = D_oo^{-1} D_oe x

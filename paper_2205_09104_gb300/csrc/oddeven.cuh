@@ -9,9 +9,8 @@ namespace coarse {
 struct EoArgs {
   const void* blocks;   // [V][5][n][n] of the block type
   const void* inv;      // [V][n][n] inverses of the diagonal blocks A_x + i mu sigma3, same type
-  const int* nb;        // [V][8]
-  const int* sites;     // [V]: the even sites in increasing order, then the odd sites
-  const int* half;      // [V]: position of each site in its parity's list
+  const int4* rec;      // [V][4] neighbour records (coarse_op::eo_rec): even list, then odd list
+  int* err;             // raised (1) if a bounded wait of the prefetching variant ran out
   int V;
   int out_par;          // parity of the output sites (0 even, 1 odd)
   const void* v;        // hop input, compressed on the other parity (nullptr: no hops)

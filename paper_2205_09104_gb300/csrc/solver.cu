@@ -598,9 +598,8 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
       EoArgs a{};
       a.blocks = op->blk[s->prec].ptr;
       a.inv = op->inv[eo_sign(op, mu_eff)][s->prec].ptr;
-      a.nb = op->nb;
-      a.sites = op->eo_sites;
-      a.half = op->eo_half;
+      a.rec = op->eo_rec;
+      a.err = op->apply_cnt + op->V;
       a.V = op->V;
       a.mode = APPLY_PLAIN;
       a.out_par = 1;  // t_o = D_oo^{-1} r_o
