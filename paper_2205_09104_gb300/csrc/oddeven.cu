@@ -521,22 +521,37 @@ __global__ void __launch_bounds__(128) k_eo_half_w(EoArgs a) {
 }
 
 // ------------------------------------------------------------------ the streamed half apply
-// Persistent variant: one CTA of 8 warps per SM walks the sites k = blockIdx.x + i * gridDim.x of
-// the output parity.  Warp w owns one hop block of every site (w < 4: F_{x,mu}, w >= 4:
-// F_{x-mu,mu} with mu = w & 3) and feeds its own shared-memory ring: lane 0 bulk-copies the block
-// and the input vector it multiplies S sites ahead, completing on the stage's mbarrier.  Thread 0
-// feeds a three-stage ring with the inverse block and the epilogue's vectors (z, base, acc).  The
-// bytes in flight per SM are then set by the rings (8 S blocks), not by registers, which keeps HBM
-// busy with few warps.  Per site: each warp reduces its block against its vector into its slot of
-// hpart; barrier; g = z - sum of the 8 slots (fixed order); u = B_x^{-1} g with the inverse's row
-// quads split over the warps; barrier; the epilogue as in k_eo_half.  A stage is refilled only
-// after its readers are done (every value read from it has been consumed): a hop stage by its own
-// warp after __syncwarp, an inverse stage one site later, after the next CTA barrier.  (A proxy
-// fence there would make the refilling thread wait for its own earlier global stores, a round
-// trip per site on the critical path.)  Every wait is bounded; an
-// expired wait ends the loop for the whole CTA (the barriers are __syncthreads_or), raises *err
-// and drains the copies still in flight with bounded waits.  Needs v and 16-byte aligned vectors.
-constexpr int kEoRingWarps = 8, kEoInvStages = 3, kEoRingMaxS = 6;
+// Persistent, warp-specialised variant: one CTA per SM takes a contiguous range of the output
+// parity's sites and streams them through a ring of S shared-memory stages.  A stage holds one
+// site's operands: its 4 forward blocks (contiguous in memory: one bulk copy), the 4 neighbours'
+// forward blocks used as backward hops, its inverse block, the 8 neighbour vectors the hops
+// multiply and the epilogue's z, base, acc.  A producer warp reads the sites' neighbour records
+// (8 sites per warp-wide load) and issues every copy, completing on the stage's "full" mbarrier,
+// as soon as the consumers have released the stage on its "empty" mbarrier.  The 8 consumer
+// warps touch no global memory but the output: warp w reduces one hop block (w < 4: F_{x,mu},
+// w >= 4: F_{x-mu,mu}, mu = w & 3) against its vector into its slot of hpart; barrier;
+// g = z - sum of the 8 slots (fixed order); u = B_x^{-1} g with the inverse's row quads split over
+// the warps, the epilogue's operands read into registers; barrier; release; the epilogue as in
+// k_eo_half.  The consumers synchronise on named barrier 1 (256 threads) so that the producer
+// runs ahead.  The bytes in flight per SM are set by the ring (up to S sites), not by registers.
+// Every wait is bounded: an expired consumer wait ends the loop for all consumers (the first
+// barrier is a reduction) and raises *err; an expired producer wait stops the producer, which
+// then drains its copies still in flight (bounded waits).  Needs v and 16-byte aligned vectors.
+constexpr int kEoRingWarps = 8, kEoRingMaxS = 6;
+constexpr uint32_t kEoRingThreads = 32 * (kEoRingWarps + 1);
+
+__device__ __forceinline__ int consumers_red_or(int pred) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n barrier.cta.red.or.pred q, 1, %2, p;\n selp.s32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(pred), "n"(32 * kEoRingWarps)
+      : "memory");
+  return r;
+}
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("barrier.cta.sync 1, %0;" ::"n"(32 * kEoRingWarps) : "memory");
+}
 
 // Block-row chunk from shared memory.  For 32-byte chunks (FP32, n = 32) lanes 4..7 of each
 // quarter warp take the two 16-byte halves in the opposite order, so that the 8 lanes of a
@@ -567,115 +582,129 @@ __device__ __forceinline__ void ring_row(const BT* p, int t, AC (&e)[CPL]) {
   }
 }
 
+// Shared-memory bytes of one stage of the streamed layout.
+template <int N, class BT, class VT>
+constexpr size_t eo_ring_stage_bytes() {
+  return 9 * (size_t)N * N * sizeof(BT) + 11 * (size_t)N * sizeof(VT);
+}
+
 template <int N, class BT, class VT, class AC>
-__global__ void __launch_bounds__(32 * kEoRingWarps, 1) k_eo_ring(EoArgs a, int S) {
-  constexpr int CPL = N / 8, KR = N / 4, NV = N / 2, NI = kEoInvStages;
+__global__ void __launch_bounds__(kEoRingThreads, 1) k_eo_ring(EoArgs a, int S) {
+  constexpr int CPL = N / 8, KR = N / 4, NV = N / 2;
   constexpr size_t BSZ = (size_t)N * N;
   constexpr uint32_t BB = (uint32_t)(BSZ * sizeof(BT)), VB = (uint32_t)(N * sizeof(VT));
-  constexpr uint32_t HS = BB + VB, IS = BB + 3 * VB;  // hop and inverse stage bytes
+  constexpr uint32_t SB = (uint32_t)eo_ring_stage_bytes<N, BT, VT>();
+  constexpr uint32_t VO = 9 * BB;  // vector slots: 8 hop vectors (slot = consumer warp), z, base, acc
   using AT = decltype(AC{}.x);
   extern __shared__ __align__(128) unsigned char ring_smem[];
   __shared__ AC hpart[kEoRingWarps][N];
   __shared__ AC us[N];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 3, t = lane & 7;
-  const int mu = wid & 3;
-  const bool bwd = wid >= 4;
-  const int nh = a.V / 2, G = gridDim.x, k0 = blockIdx.x;
-  if (k0 >= nh) return;  // CTA-uniform
+  const int nh = a.V / 2, G = gridDim.x;
+  const int s0 = (int)((long long)nh * blockIdx.x / G), s1 = (int)((long long)nh * (blockIdx.x + 1) / G);
+  const int cnt = s1 - s0;  // sites of this CTA (CTA-uniform)
+  if (cnt <= 0) return;
   if (a.stop && *a.stop) return;
-  unsigned char* hop = ring_smem + (size_t)wid * S * HS;
-  unsigned char* invs = ring_smem + (size_t)kEoRingWarps * S * HS;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(invs + (size_t)NI * IS);
-  uint64_t* hb = bars + wid * S;               // this warp's hop stages
-  uint64_t* ib = bars + kEoRingWarps * S;      // inverse stages
-  const int cnt = (nh - k0 + G - 1) / G;       // sites of this CTA
-  const int4* R = a.rec + (size_t)a.out_par * nh * 4;
-  const BT* B = static_cast<const BT*>(a.blocks);
-  const BT* INV = static_cast<const BT*>(a.inv);
-  const VT* v = static_cast<const VT*>(a.v);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring_smem + (size_t)S * SB);
+  uint64_t* empty = full + S;
   const VT* z = static_cast<const VT*>(a.z);
   const VT* base = static_cast<const VT*>(a.base);
   VT* acc = static_cast<VT*>(a.acc);
   const bool acc_in = a.mode != APPLY_PLAIN && a.mode != APPLY_POLY_FIRST;
-  const uint32_t inv_tx = BB + (z ? VB : 0u) + (base ? VB : 0u) + (acc_in ? VB : 0u);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kEoRingWarps * S + NI; ++i) mbar_init(bars + i, 1);
+    for (int i = 0; i < S; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // ring feeders: site i of this CTA into stage i % S (hop) or i % NI (inverse)
-  auto issue_hop = [&](int i, int4 q) {
-    uint64_t* bar = hb + i % S;
-    unsigned char* st = hop + (size_t)(i % S) * HS;
-    mbar_expect_tx(bar, HS);
-    const size_t owner = bwd ? (size_t)q.y : (size_t)q.w;
-    bulk_g2s(st, B + (owner * 5 + 1 + mu) * BSZ, BB, bar);
-    bulk_g2s(st + BB, v + (size_t)(bwd ? q.z : q.x) * N, VB, bar);
-  };
-  auto issue_inv = [&](int i, int x) {
-    const size_t k = (size_t)k0 + (size_t)i * G;
-    uint64_t* bar = ib + i % NI;
-    unsigned char* st = invs + (size_t)(i % NI) * IS;
-    mbar_expect_tx(bar, inv_tx);
-    bulk_g2s(st, INV + (size_t)x * BSZ, BB, bar);
-    if (z) bulk_g2s(st + BB, z + k * N, VB, bar);
-    if (base) bulk_g2s(st + BB + VB, base + k * N, VB, bar);
-    if (acc_in) bulk_g2s(st + BB + 2 * VB, acc + k * N, VB, bar);
-  };
-  int hop_issued = 0, inv_issued = 0;
-  if (lane == 0) {
-    int4 q[kEoRingMaxS];
+
+  if (wid == kEoRingWarps) {
+    // ---- producer warp
+    const int4* R = a.rec + ((size_t)a.out_par * nh + s0) * 4;
+    const BT* B = static_cast<const BT*>(a.blocks);
+    const BT* INV = static_cast<const BT*>(a.inv);
+    const VT* v = static_cast<const VT*>(a.v);
+    const uint32_t tx = 9 * BB + 8 * VB + (z ? VB : 0u) + (base ? VB : 0u) + (acc_in ? VB : 0u);
+    int issued = 0;
+    bool ok = true;
+    for (int j0 = 0; j0 < cnt && ok; j0 += 8) {
+      // lane l: the record of site j0 + l / 4, direction l % 4
+      int4 q = make_int4(0, 0, 0, 0);
+      if (j0 + lane / 4 < cnt) q = __ldg(R + (size_t)j0 * 4 + lane);
+      for (int jj = 0; jj < 8 && j0 + jj < cnt; ++jj) {
+        int4 qm[4];
 #pragma unroll
-    for (int i = 0; i < kEoRingMaxS; ++i)
-      if (i < S && i < cnt) q[i] = __ldg(R + ((size_t)k0 + (size_t)i * G) * 4 + mu);
+        for (int m = 0; m < 4; ++m) {
+          qm[m].x = __shfl_sync(0xffffffffu, q.x, jj * 4 + m);
+          qm[m].y = __shfl_sync(0xffffffffu, q.y, jj * 4 + m);
+          qm[m].z = __shfl_sync(0xffffffffu, q.z, jj * 4 + m);
+          qm[m].w = __shfl_sync(0xffffffffu, q.w, jj * 4 + m);
+        }
+        const int j = j0 + jj;
+        if (lane == 0) {
+          // stage j % S is free once the consumers released its previous site j - S
+          if (j >= S) ok = mbar_wait(empty + j % S, (uint32_t)((j / S - 1) & 1));
+          if (ok) {
+            const size_t k = (size_t)s0 + j;
+            uint64_t* bar = full + j % S;
+            unsigned char* st = ring_smem + (size_t)(j % S) * SB;
+            const size_t x = (size_t)qm[0].w;
+            mbar_expect_tx(bar, tx);
+            bulk_g2s(st, B + (x * 5 + 1) * BSZ, 4 * BB, bar);
 #pragma unroll
-    for (int i = 0; i < kEoRingMaxS; ++i)
-      if (i < S && i < cnt) issue_hop(i, q[i]);
-    hop_issued = min(S, cnt);
+            for (int m = 0; m < 4; ++m)
+              bulk_g2s(st + (4 + m) * BB, B + ((size_t)qm[m].y * 5 + 1 + m) * BSZ, BB, bar);
+            bulk_g2s(st + 8 * BB, INV + x * BSZ, BB, bar);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              bulk_g2s(st + VO + m * VB, v + (size_t)qm[m].x * N, VB, bar);
+              bulk_g2s(st + VO + (4 + m) * VB, v + (size_t)qm[m].z * N, VB, bar);
+            }
+            if (z) bulk_g2s(st + VO + 8 * VB, z + k * N, VB, bar);
+            if (base) bulk_g2s(st + VO + 9 * VB, base + k * N, VB, bar);
+            if (acc_in) bulk_g2s(st + VO + 10 * VB, acc + k * N, VB, bar);
+            ++issued;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+      }
+    }
+    if (!ok && lane == 0) {
+      // the consumers stopped: drain the copies still in flight (the last S issued)
+      atomicExch(a.err, 1);
+      for (int j = max(0, issued - S); j < issued; ++j) mbar_wait(full + j % S, (uint32_t)((j / S) & 1));
+    }
+    return;
   }
-  if (threadIdx.x == 0) {
-    int xs[NI];
-#pragma unroll
-    for (int i = 0; i < NI; ++i)
-      if (i < cnt) xs[i] = __ldg(R + ((size_t)k0 + (size_t)i * G) * 4).w;
-#pragma unroll
-    for (int i = 0; i < NI; ++i)
-      if (i < cnt) issue_inv(i, xs[i]);
-    inv_issued = min(NI, cnt);
-  }
+
+  // ---- consumer warps
+  const int g = lane >> 3, t = lane & 7;
+  const bool bwd = wid >= 4;
   const AT st = (t * CPL < NV) ? AT(1) : AT(-1);  // sigma3 of this lane's columns
   const double2 c0d = a.mode != APPLY_PLAIN ? a.coef[0] : make_double2(0.0, 0.0);
   const double2 c1d = a.mode != APPLY_PLAIN ? a.coef[1] : make_double2(0.0, 0.0);
   const double2 c2d = a.mode == APPLY_POLY_FIRST ? a.coef[2] : make_double2(0.0, 0.0);
   const AC c0{AT(c0d.x), AT(c0d.y)}, c1{AT(c1d.x), AT(c1d.y)}, c2{AT(c2d.x), AT(c2d.y)};
   VT* y = static_cast<VT*>(a.y);
-  bool failed = false;
-  int i = 0;
-  // records for the refills, loaded one iteration before their use: iteration i refills the hop
-  // stage with site i + S and the inverse stage with site i - 1 + NI
-  int4 qn = make_int4(0, 0, 0, 0);
-  int xn = 0;
-  if (lane == 0 && S < cnt) qn = __ldg(R + ((size_t)k0 + (size_t)S * G) * 4 + mu);
-  for (; i < cnt; ++i) {
-    const size_t k = (size_t)k0 + (size_t)i * G;
-    int4 qnn = make_int4(0, 0, 0, 0);
-    if (lane == 0 && i + 1 + S < cnt) qnn = __ldg(R + ((size_t)k0 + (size_t)(i + 1 + S) * G) * 4 + mu);
-    int xnn = 0;
-    if (threadIdx.x == 0 && i + NI < cnt) xnn = __ldg(R + ((size_t)k0 + (size_t)(i + NI) * G) * 4).w;
+  const int ne = threadIdx.x;  // epilogue element of this thread (if < N)
+  for (int i = 0; i < cnt; ++i) {
+    const size_t k = (size_t)s0 + i;
     // warp-uniform outcome (the shuffles below need the whole warp)
-    bool ok = __all_sync(0xffffffffu, mbar_wait(hb + i % S, (uint32_t)((i / S) & 1)));
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(full + i % S, (uint32_t)((i / S) & 1)));
+    const unsigned char* sp = ring_smem + (size_t)(i % S) * SB;
     if (ok) {
-      const unsigned char* sp = hop + (size_t)(i % S) * HS;
-      const BT* blk = reinterpret_cast<const BT*>(sp) + g * N + t * CPL;
-      const VT* vec = reinterpret_cast<const VT*>(sp + BB);
+      const BT* blk = reinterpret_cast<const BT*>(sp + (size_t)wid * BB) + g * N + t * CPL;
+      const VT* vec = reinterpret_cast<const VT*>(sp + VO + (size_t)wid * VB);
       if (!bwd) {
         // row sums of F_{x,mu} v_{x+mu}
         AC w[CPL], yf[KR];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-          const VT vv = vec[t * CPL + c];
-          w[c] = AC{AT(vv.x), AT(vv.y)};
+          const VT e = vec[t * CPL + c];
+          w[c] = AC{AT(e.x), AT(e.y)};
         }
 #pragma unroll
         for (int r = 0; r < KR; ++r) {
@@ -702,9 +731,9 @@ __global__ void __launch_bounds__(32 * kEoRingWarps, 1) k_eo_ring(EoArgs a, int 
         for (int c = 0; c < CPL; ++c) yb[c] = AC{0, 0};
 #pragma unroll
         for (int r = 0; r < KR; ++r) {
-          const VT vv = vec[4 * r + g];
+          const VT e = vec[4 * r + g];
           const AT sk = (4 * r + g < NV) ? AT(1) : AT(-1);
-          const AC xr{sk * AT(vv.x), sk * AT(vv.y)};
+          const AC xr{sk * AT(e.x), sk * AT(e.y)};
           AC f[CPL];
           ring_row<AC, BT, CPL>(blk + (size_t)r * 4 * N, t, f);
 #pragma unroll
@@ -722,42 +751,28 @@ __global__ void __launch_bounds__(32 * kEoRingWarps, 1) k_eo_ring(EoArgs a, int 
           for (int c = 0; c < CPL; ++c) hpart[wid][t * CPL + c] = cscale(yb[c], st);
       }
     }
-    // the warp's reads of this stage are complete (their values are in hpart): refill it
-    __syncwarp();
-    if (ok && lane == 0 && i + S < cnt) {
-      issue_hop(i + S, qn);
-      ++hop_issued;
+    if (consumers_red_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(a.err, 1);
+      return;  // all consumers; the producer drains its copies
     }
-    qn = qnn;
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    // every thread is past the epilogue of site i - 1: its inverse stage takes site i - 1 + NI
-    if (threadIdx.x == 0 && i >= 1 && i - 1 + NI < cnt) {
-      issue_inv(i - 1 + NI, xn);
-      ++inv_issued;
-    }
-    xn = xnn;
-    ok = __all_sync(0xffffffffu, mbar_wait(ib + i % NI, (uint32_t)((i / NI) & 1)));
-    const unsigned char* ip = invs + (size_t)(i % NI) * IS;
-    const VT* sv = reinterpret_cast<const VT*>(ip + BB);  // z, base, acc
-    if (ok) {
+    AC bv{0, 0}, av{0, 0};
+    {
+      const VT* sv = reinterpret_cast<const VT*>(sp + VO + 8 * (size_t)VB);  // z, base, acc
       AC gi[CPL];
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
         const int j = t * CPL + c;
         AC hv = hpart[0][j];
 #pragma unroll
-        for (int q = 1; q < kEoRingWarps; ++q) hv = cadd(hv, hpart[q][j]);
+        for (int w = 1; w < kEoRingWarps; ++w) hv = cadd(hv, hpart[w][j]);
         if (z) {
-          const VT zv = sv[j];
-          gi[c] = AC{AT(zv.x) - hv.x, AT(zv.y) - hv.y};
+          const VT e = sv[j];
+          gi[c] = AC{AT(e.x) - hv.x, AT(e.y) - hv.y};
         } else {
           gi[c] = hv;
         }
       }
-      const BT* iblk = reinterpret_cast<const BT*>(ip) + g * N + t * CPL;
+      const BT* iblk = reinterpret_cast<const BT*>(sp + 8 * (size_t)BB) + g * N + t * CPL;
       for (int q = wid; q < KR; q += kEoRingWarps) {
         AC e[CPL];
         ring_row<AC, BT, CPL>(iblk + (size_t)q * 4 * N, t, e);
@@ -771,20 +786,24 @@ __global__ void __launch_bounds__(32 * kEoRingWarps, 1) k_eo_ring(EoArgs a, int 
         }
         if (t == 0) us[4 * q + g] = uf;
       }
-    }
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    for (int e = threadIdx.x; e < N; e += blockDim.x) {
-      const size_t idx = k * N + e;
-      AC r = us[e];
-      AC xs{0, 0};
-      if (base) {
-        const VT bv = sv[N + e];
-        xs = AC{AT(bv.x), AT(bv.y)};
-        r = csub(xs, r);
+      if (ne < N) {
+        if (base) {
+          const VT e = sv[N + ne];
+          bv = AC{AT(e.x), AT(e.y)};
+        }
+        if (acc_in) {
+          const VT e = sv[2 * N + ne];
+          av = AC{AT(e.x), AT(e.y)};
+        }
       }
+    }
+    consumers_sync();
+    // every consumer is done with the stage: release it to the producer
+    if (threadIdx.x == 0) mbar_arrive(empty + i % S);
+    if (ne < N) {
+      const size_t idx = k * N + ne;
+      AC r = us[ne];
+      if (base) r = csub(bv, r);
       if (a.mode == APPLY_PLAIN) {
         VT o;
         o.x = r.x;
@@ -792,33 +811,19 @@ __global__ void __launch_bounds__(32 * kEoRingWarps, 1) k_eo_ring(EoArgs a, int 
         y[idx] = o;
       } else {
         // chain step on S: s' = x - c0 (S x) ; acc = acc + c1 s'  (first: acc = c2 x + c1 s')
-        AC ac;
-        if (a.mode == APPLY_POLY_FIRST) {
-          ac = cmul(c2, xs);
-        } else {
-          const VT av = sv[2 * N + e];
-          ac = AC{AT(av.x), AT(av.y)};
-        }
-        const AC spv = csub(xs, cmul(c0, r));
-        ac = cadd(ac, cmul(c1, spv));
+        AC acv = a.mode == APPLY_POLY_FIRST ? cmul(c2, bv) : av;
+        const AC spv = csub(bv, cmul(c0, r));
+        acv = cadd(acv, cmul(c1, spv));
         VT o;
         o.x = spv.x;
         o.y = spv.y;
         y[idx] = o;
         VT ao;
-        ao.x = ac.x;
-        ao.y = ac.y;
+        ao.x = acv.x;
+        ao.y = acv.y;
         acc[idx] = ao;
       }
     }
-  }
-  if (failed) {
-    // drain: each stage holds at most one outstanding copy group, the last S (NI) issued
-    if (threadIdx.x == 0) atomicExch(a.err, 1);
-    if (lane == 0)
-      for (int j = max(i, hop_issued - S); j < hop_issued; ++j) mbar_wait(hb + j % S, (uint32_t)((j / S) & 1));
-    if (threadIdx.x == 0)
-      for (int j = max(i, inv_issued - NI); j < inv_issued; ++j) mbar_wait(ib + j % NI, (uint32_t)((j / NI) & 1));
   }
 }
 
@@ -905,12 +910,11 @@ int eo_prepare(coarse_op* op, double mu_eff, cudaStream_t s) {
 
 namespace {
 
-// The streamed layout: S hop stages per warp, as many as fit next to the inverse ring (at most
-// kEoRingMaxS); one CTA per SM.  INVALID_ARG if not even one stage fits.
+// The streamed layout: S stages of one site's operands, as many as fit (at most kEoRingMaxS); one
+// CTA per SM.  INVALID_ARG if not even one stage fits.
 template <int N, class BT, class VT, class AC>
 int launch_eo_ring_n(const EoArgs& a, cudaStream_t s) {
-  constexpr size_t HS = (size_t)N * N * sizeof(BT) + N * sizeof(VT);
-  constexpr size_t IS = (size_t)N * N * sizeof(BT) + 3 * N * sizeof(VT);
+  constexpr size_t SB = eo_ring_stage_bytes<N, BT, VT>();
   static int S = -1;
   static size_t dyn = 0;
   if (S < 0) {
@@ -919,10 +923,10 @@ int launch_eo_ring_n(const EoArgs& a, cudaStream_t s) {
     COARSE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa{};
     COARSE_CUDA(cudaFuncGetAttributes(&fa, k_eo_ring<N, BT, VT, AC>));
-    // the rings and mbarriers, next to the static shared memory and the dynamic part's alignment
+    // the ring and its mbarriers, next to the static shared memory and the dynamic part's alignment
     int sv = kEoRingMaxS;
     for (; sv >= 1; --sv) {
-      dyn = (size_t)kEoRingWarps * sv * HS + kEoInvStages * IS + 8 * (size_t)(kEoInvStages + kEoRingWarps * sv);
+      dyn = (size_t)sv * SB + 16 * (size_t)sv;
       if (dyn + fa.sharedSizeBytes + 128 <= (size_t)optin) break;
     }
     if (sv >= 1)
@@ -935,7 +939,7 @@ int launch_eo_ring_n(const EoArgs& a, cudaStream_t s) {
     return COARSE_ERR_INVALID_ARG;
   }
   const int grid = std::min(a.V / 2, sm_count());
-  k_eo_ring<N, BT, VT, AC><<<grid, 32 * kEoRingWarps, dyn, s>>>(a, S);
+  k_eo_ring<N, BT, VT, AC><<<grid, kEoRingThreads, dyn, s>>>(a, S);
   return COARSE_OK;
 }
 

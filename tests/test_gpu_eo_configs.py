@@ -3,10 +3,10 @@ one warp per site, one CTA of 2 warps per site with rolled or unrolled direction
 also with the inverse block and epilogue vectors prefetched into shared memory, and the streamed
 persistent layout) gives the oracle's S = 1 - D_ee^-1 D_eo D_oo^-1 D_oe, and solves through it
 reach the oracle's 1e-10: the layout is fixed through the autotuner's cache file in a
-subprocess.  The small lattices give the streamed layout one site per CTA; a coarse 8x8x8x4
-lattice (1024 sites per parity on 152 SMs) makes its CTAs walk 6-7 sites, so that every hop
-stage (3 per warp in FP32, 6 in BF16) and inverse stage is refilled and its mbarrier phase
-flips."""
+subprocess.  The small lattices give the streamed layout one site per CTA; the coarse 8^4
+lattice (2048 sites per parity on 152 SMs) makes its CTAs walk 13-14 sites, so that every stage
+(3 in FP32, 5 in BF16) is refilled several times, its mbarrier phases flip, and the producer
+reads its neighbour records in two batches of 8 sites."""
 import os
 import subprocess
 import sys
@@ -26,7 +26,7 @@ def test_eo_layout(tmp_path, variant, nv, fdims, mu):
 
 
 def test_eo_streamed_many_sites_per_cta(tmp_path):
-    _run(tmp_path, 6, 16, "16x16x16x8", 0.03)
+    _run(tmp_path, 6, 16, "16x16x16x16", 0.03)
 
 
 def _run(tmp_path, variant, nv, fdims, mu):
