@@ -237,9 +237,11 @@ def run_gb300(args):
         "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": (("k_eo_half<32,float2> x2 (operator S) + k_eo_half<32,cbf16> x2 (polynomial chain); "
-                                 "one launch = one S apply = two half passes") if args.oddeven == "on" and poly_bf16 else
-                                "k_eo_half<32,%s> x2 per S apply" % ("cbf16" if prec == cg.PREC_BF16 else "float2")
+                     "kernel": (("%s<32,float2> x2 (operator S) + %s<32,cbf16> x2 (polynomial chain); "
+                                 "one launch = one S apply = two half passes" % (eo_layout(cg, 1), eo_layout(cg, 2)))
+                                if args.oddeven == "on" and poly_bf16 else
+                                "%s<32,%s> x2 per S apply" % (eo_layout(cg, prec),
+                                                               "cbf16" if prec == cg.PREC_BF16 else "float2")
                                 if args.oddeven == "on" else
                                 "k_apply*<32,float2> (operator) + k_apply*<32,cbf16> (polynomial chain)" if poly_bf16 else
                                 f"k_apply*<32,{'cbf16' if prec == cg.PREC_BF16 else 'float2'}>"),
@@ -325,6 +327,20 @@ def cpu_baseline(host_blocks, gpu_iters):
             "sample": f"oracle FP64 pp-GMRES, {steps} Arnoldi steps (d=4: {4 * steps} applies + MGS) on one "
                       f"right-hand side; seconds per step x {iters:.0f} steps per solve ({src}); NumPy einsum, "
                       f"single thread"}
+
+
+# layouts of the odd-even half apply, by the autotuner's candidate number
+EO_LAYOUTS = {0: "k_eo_half[CTA of 4 warps]", 1: "k_eo_half_w[warp per site]", 2: "k_eo_half[CTA of 2 warps]",
+              3: "k_eo_half[CTA of 2 warps, unrolled]", 4: "k_eo_half[CTA of 2 warps, prefetch]",
+              5: "k_eo_half[CTA of 2 warps, unrolled, prefetch]", 6: "k_eo_ring[streamed]"}
+
+
+def eo_layout(cg, prec):
+    """Name of the half-apply layout the autotuner chose for block precision `prec` (n = 32)."""
+    for line in cg.autotune_report().splitlines():
+        if line.startswith(f"eo/p{prec}/n32/") and "->" in line:
+            return EO_LAYOUTS.get(int(line.split("->")[1].split()[0]), "k_eo_half")
+    return "k_eo_half"
 
 
 def run_reference(args):
