@@ -17,6 +17,9 @@ Modules and the passages they follow:
                the GMRES polynomial (Sec. 3.3), Leja ordering (Alg. 2),
                polynomially preconditioned GMRES (Alg. 3), GCRO-DR (Sec. 3.4)
     gradient   adjoint solve and block gradients (Sec. 4.2: Q = Gamma5 D is Hermitian)
+    oddeven    odd-even reduced system with block-Jacobi preconditioning (Sec. 2, 3.2)
+    pipelined  latency-1 pipelined GMRES and GCRO-DR (Sec. 3.5, Alg. "pipe1fgmres",
+               "pipe1gcrodr")
 
 Every function is pinned by the ``-m "not gpu"`` tests to something other than
 itself: closed forms, exact identities, brute force, or dense LU.  Functions
