@@ -183,10 +183,16 @@ __global__ void __launch_bounds__(32 * W, eo_min_blocks<N, AC, W, PF>()) k_eo_ha
   const VT* z = static_cast<const VT*>(a.z);
   const VT* base = static_cast<const VT*>(a.base);
   const bool acc_in = a.mode != APPLY_PLAIN && a.mode != APPLY_POLY_FIRST;
+  if constexpr (PF) {
+    // the mbarrier is initialised before any thread can wait on it
+    if (threadIdx.x == 0) {
+      mbar_init(&sbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
   if (PF && threadIdx.x == 0) {
     constexpr uint32_t ib = (uint32_t)(BSZ * sizeof(BT)), vb = (uint32_t)(N * sizeof(VT));
-    mbar_init(&sbar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     mbar_expect_tx(&sbar, ib + (z ? vb : 0u) + (base ? vb : 0u) + (acc_in ? vb : 0u));
     bulk_g2s(sinv, static_cast<const BT*>(a.inv) + (size_t)x * BSZ, ib, &sbar);
     if (z) bulk_g2s(svec, z + (size_t)k * N, vb, &sbar);
