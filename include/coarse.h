@@ -124,6 +124,9 @@ int coarse_apply_adjoint(const coarse_op* op, const void* x, void* y, int nrhs, 
  *        (x0 + x1 + x2 + x3) mod 2), complex128 for FP64, complex64 otherwise; no overlap.
  * Needs even lattice extents.  Asynchronous, except that the first call (and the
  * first after coarse_op_update) computes the inverses and synchronises `stream`.
+ * The staged layouts of the half apply wait on their copies with bounded waits; if
+ * one ran out, y is incomplete and the next synchronising call on the operator
+ * returns COARSE_ERR_TIMEOUT, as for coarse_apply.
  */
 int coarse_schur_apply(coarse_op* op, const void* x, void* y, int precision, void* stream);
 
