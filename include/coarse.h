@@ -151,11 +151,15 @@ int coarse_residual(const coarse_op* op, const void* b, const void* x, void* r, 
  * The paper has no counterpart of this call.
  * Limit: V*n <= 131072 unknowns; larger operators get COARSE_ERR_INVALID_ARG.
  * The array is looked up once per device (cudaGetSymbolAddress) on the first
- * call made with that device current; make that first call before any stream
- * capture.  Every call shares the array, which keeps the previous call's
- * contents (the counters that must start at zero are cleared at the start of
- * each call): calls that overlap on the GPU, from any stream or thread, race and
- * must not be issued.  Synchronises `stream`.
+ * call made with that device current, and that first call also writes the
+ * array's constant part with a synchronous copy: make it before any stream
+ * capture.  The call itself reads its result back and synchronises `stream`, so
+ * it must never be issued while `stream` is being captured; it then returns
+ * COARSE_ERR_INVALID_ARG.  Every call shares the array, which keeps the previous
+ * call's contents (the counters that must start at zero are cleared at the start
+ * of each call): calls that overlap on the GPU, from any stream or thread, race
+ * and must not be issued.  COARSE_ERR_TIMEOUT if a bounded wait of a staged
+ * stencil kernel ran out during the call (r is then incomplete).
  */
 int coarse_residual_noalloc(const coarse_op* op, const void* b, const void* x, void* r, double* norms_host,
                             void* stream);
@@ -184,6 +188,13 @@ int coarse_residual_noalloc(const coarse_op* op, const void* b, const void* x, v
  * system sigma3 D_c(-mu) sigma3 the same way.  The first use (per sign of mu) computes the
  * inverses of the diagonal blocks A_x + i mu sigma3 in FP64. */
 #define COARSE_ODD_EVEN 0x20u
+/* GCRO-DR (Sec. 3.4) builds its first recycle space from the harmonic Ritz vectors of a plain
+ * GMRES(m) cycle, which needs more than k Arnoldi steps.  With this flag, while the solver holds no
+ * recycle space (and defl_k > 0), every cycle runs all m steps instead of ending when its
+ * least-squares residual reaches the inner target, so that the first cycle yields k vectors even
+ * when the system would converge sooner; the extra steps only refine that cycle's correction.
+ * Meant for a setup solve; later solves reuse the space without the flag. */
+#define COARSE_RECYCLE_FULL_CYCLE 0x40u
 
 typedef struct {
   int32_t m;               /* restart length of GMRES / GCRO-DR (Sec. 3.1), 2 .. 64 */
@@ -196,7 +207,8 @@ typedef struct {
   double inner_tol;        /* relative residual target of each inner solve (FP32/BF16 only) */
   int32_t max_ir;          /* FP64 iterative-refinement steps allowed */
   uint32_t flags;          /* COARSE_ZERO_GUESS | COARSE_REBUILD_POLY | COARSE_RESET_RECYCLE |
-                              COARSE_TIME_APPLY | COARSE_POLY_BF16 */
+                              COARSE_TIME_APPLY | COARSE_POLY_BF16 | COARSE_ODD_EVEN |
+                              COARSE_RECYCLE_FULL_CYCLE */
   uint64_t seed;           /* seeds the polynomial start vector when poly_start is NULL */
   const void* poly_start;  /* optional device complex128 [V][n]: start vector of the polynomial's Arnoldi */
 } coarse_solve_params;
@@ -215,7 +227,11 @@ typedef struct {
   int32_t apply_count;     /* stencil launches timed in apply_ms */
   int32_t kernel_launches; /* kernels this call launched */
   double apply_bytes;      /* algorithmic bytes of the stencil launches timed in apply_ms
-                              (5 n^2 V block bytes + 2 N vector bytes each, by their precision) */
+                              (5 n^2 V block bytes + 2 N vector bytes each, by their precision;
+                              odd-even S applies: 9 n^2 V block bytes + 2.5 (V n) vector bytes) */
+  double apply_ms_prec[3];    /* apply_ms split by the block precision of the launch (coarse_precision) */
+  double apply_bytes_prec[3]; /* apply_bytes, split the same way */
+  int32_t apply_count_prec[3];/* apply_count, split the same way */
 } coarse_solve_info;
 
 /*
@@ -252,6 +268,10 @@ int coarse_solve_adjoint(coarse_op* op, const void* b, void* x, int nrhs, const 
  * graph and replayed.  ops[i], b[i], x[i], nrhs[i] as in coarse_solve; all
  * operators use the same params.  infos: host array of sum(nrhs) records in
  * (operator, column) order.  Synchronises `stream`.
+ * Each solve follows Sec. 3.6 exactly as coarse_solve does (restarted GMRES,
+ * polynomial of Sec. 3.3, GCRO-DR of Sec. 3.4, FP64 refinement); the batching
+ * itself has no counterpart in the paper, which solves one coarsest system at a
+ * time, distributed over many processes.
  */
 int coarse_solve_batched(coarse_op* const* ops, int nops, const void* const* b, void* const* x,
                          const int* nrhs, const coarse_solve_params* params, coarse_solve_info* infos,
@@ -261,12 +281,19 @@ int coarse_solve_batched(coarse_op* const* ops, int nops, const void* const* b, 
  * coarse_block_grad -- block gradients of a real loss L through x = D_c^{-1} b
  * given lambda = D_c^{-H} dL/dx*:  G_self[x] = -lambda_x x_x^H and
  * G_hop[x][d] = -lambda_x x_{x +- mu_d}^H (convention dL = Re sum conj(G) dD).
- * lambda, x : device complex128 [V][n];  g_self : device complex128 [V][n][n];
- * g_hop : device complex128 [V][8][n][n] (canonical 9-block layout).
+ * The paper has no counterpart (it never differentiates the coarse solve); the
+ * adjoint solve that provides lambda uses D_c^H = sigma3 D_c(-mu) sigma3, the
+ * coarse form of the Gamma5-hermiticity of Sec. 4.2.
+ * lambda, x : device complex128 [V][n];  g_self : device complex128 [V][n][n].
+ * hop_dirs  : 8 -> g_hop is [V][8][n][n] (canonical 9-block layout, every hop block an
+ *             independent input);  4 -> g_hop is [V][4][n][n], the gradient with respect to
+ *             the forward blocks of a COARSE_ASSUME_GAMMA5 input, whose backward hops
+ *             sigma3 F^H sigma3 are derived from them: the backward-hop gradient of x + mu is
+ *             folded onto F_{x,mu} as sigma3 G^H sigma3.
  * Asynchronous on `stream`.
  */
 int coarse_block_grad(const coarse_op* op, const void* lambda, const void* x, void* g_self, void* g_hop,
-                      void* stream);
+                      int hop_dirs, void* stream);
 
 /*
  * coarse_op_poly -- the Leja-ordered harmonic Ritz values theta_1..theta_d
@@ -287,6 +314,56 @@ int coarse_op_poly(const coarse_op* op, int precision, double* theta_host, int c
  * buf : host char[len]; receives a NUL-terminated (possibly truncated) report.
  */
 int coarse_autotune_report(char* buf, long long len);
+
+/*
+ * coarse_autotune_set -- fixes the launch configuration for one kernel family and shape
+ * instead of timing the candidates, e.g. to reproduce a measurement or a result bit for bit
+ * across processes.  key: a key as coarse_autotune_report prints it ("eo/p1/n48/v15"), with or
+ * without its GPU-model suffix ("@sm103x152"); without it the decision applies to every device.
+ * (a, b, c): the configuration, as in the report; a < 0 forgets the decision instead, so that
+ * the next launch times the candidates again.  Takes effect from the next launch.  The paper
+ * has no counterpart.
+ */
+int coarse_autotune_set(const char* key, int a, int b, int c);
+
+/*
+ * coarse_recycle_check -- re-evaluates the GCRO-DR recycle space that the handle holds for one
+ * inner system (Sec. 3.4: U_k, C_k with A U_k = C_k and C_k^H C_k = I, where A = D q(D) is the
+ * right-preconditioned operator of the solves that built it, Sec. 3.3).  One application of A per
+ * column, polynomial chain included, in the inner precision of those solves.
+ * precision : inner precision of the solves (coarse_precision).
+ * odd_even  : 0 = the full-operator system, 1 = the odd-even reduced system (COARSE_ODD_EVEN),
+ *             where D stands for S = 1 - D_ee^{-1} D_eo D_oo^{-1} D_oe.
+ * adjoint   : 1 = the system of coarse_solve_adjoint (the same as the forward one when mu = 0).
+ * out_host  : host double[4] receiving max_i ||A u_i - c_i|| / ||c_i||, max_ij |(C^H C - I)_ij|,
+ *             k (columns held; 0 and zero defects if no recycle space was formed) and the number
+ *             of recycle-space updates made.
+ * Synchronises `stream`; uses the solver's own work vectors (do not overlap it with a solve on the
+ * same handle).
+ */
+int coarse_recycle_check(coarse_op* op, int precision, int odd_even, int adjoint, double* out_host, void* stream);
+
+/*
+ * coarse_recycle_get -- copies out the recycle space named as in coarse_recycle_check
+ * (Sec. 3.4: U_k and C_k = A U_k, C_k^H C_k = I), e.g. to inspect it or to keep it with a
+ * checkpoint of the multigrid setup.
+ * u, c : device buffers of cap columns each, [cap][N] complex128 for FP64 solves and complex64
+ *        otherwise, N = V n (full operator) or V n / 2 (odd-even reduced system, even sites in
+ *        increasing site order).  Only the first *k columns are written.
+ * *k   : receives the number of columns held (0: none, and u, c may then be NULL).
+ * Returns COARSE_ERR_INVALID_ARG if cap is below the number held.  Synchronises `stream`.
+ */
+int coarse_recycle_get(coarse_op* op, int precision, int odd_even, int adjoint, void* u, void* c, int cap, int* k,
+                       void* stream);
+
+/*
+ * coarse_measure_fp64_fma -- FP64 FMA throughput of the current device in TFLOP/s, from a plain
+ * loop of independent FMA chains (8 CTAs of 256 threads per SM, `iters` FMAs per chain, best of
+ * three timed launches on `stream`, which it synchronises).  The FP64 stencil that computes the
+ * refinement residual is bound by this rate on GB300, and this is the peak its roofline uses.
+ * The paper has no counterpart.
+ */
+int coarse_measure_fp64_fma(int iters, double* tflops_host, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* coarse_last_error(void);

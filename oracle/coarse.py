@@ -39,6 +39,29 @@ def apply(self_b: np.ndarray, hop_b: np.ndarray, dims, v: np.ndarray, mu: float 
     return y.reshape(v.shape)
 
 
+def apply_at(blocks_of, dims, v: np.ndarray, sites, mu: float = 0.0) -> np.ndarray:
+    """(D_c v)_x at the listed sites only, by the definition above.
+
+    blocks_of(x) returns (A_x, hop[x]): the n x n self block and the [8, n, n] hop blocks of
+    site x, so a caller can hand over the blocks of just the sites asked for.  v is the
+    whole vector (V*n,).  Returns [len(sites), n].
+    """
+    nb = neighbours(dims)
+    V = volume(dims)
+    vv = v.reshape(V, -1)
+    n = vv.shape[1]
+    out = np.zeros((len(sites), n), dtype=np.complex128)
+    for i, x in enumerate(sites):
+        A, hop = blocks_of(int(x))
+        y = A @ vv[x]
+        for d in range(8):
+            y = y + hop[d] @ vv[nb[x, d]]
+        if mu != 0.0:
+            y = y + 1j * mu * sigma3(n // 2) * vv[x]
+        out[i] = y
+    return out
+
+
 def apply_adjoint(self_b, hop_b, dims, v, mu: float = 0.0):
     """y = D_c^H v, from the definition (sum over the transposed couplings)."""
     V, n, _ = self_b.shape

@@ -104,3 +104,41 @@ def retrieve(self_b, hop_b, dims, x_e: np.ndarray, b: np.ndarray, mu: float = 0.
     x[ev] = x_e.reshape(-1, n)
     x[od] = x_o.reshape(-1, n)
     return x.reshape(-1)
+
+
+def schur_at(blocks_of, dims, v_e: np.ndarray, sites_e, mu: float = 0.0, inv_of=None) -> np.ndarray:
+    """(S v)_x at the listed even sites only, S = 1 - D_ee^{-1} D_eo D_oo^{-1} D_oe, from the
+    same definition as ``schur_apply``: for each odd neighbour o of x,
+    t_o = (A_o + i mu sigma3)^{-1} sum_d hop[o, d] v_{o +- mu_d}, then
+    (S v)_x = v_x - (A_x + i mu sigma3)^{-1} sum_d hop[x, d] t_{x +- mu_d}.
+    blocks_of(x) returns (A_x, hop[x]) as in coarse.apply_at; v_e is the whole compressed even
+    vector.  inv_of(x), if given, supplies the diagonal-block inverse of site x (for instance a
+    rounded copy) instead of inverting A_x + i mu sigma3.  Returns [len(sites_e), n]."""
+    par = parity(dims)
+    nb = neighbours(dims)
+    half = np.zeros(par.size, dtype=np.int64)
+    for p in (0, 1):
+        xs = np.flatnonzero(par == p)
+        half[xs] = np.arange(xs.size)
+    ve = v_e.reshape(-1, blocks_of(int(sites(dims, 0)[0]))[0].shape[0])
+    n = ve.shape[1]
+
+    def diag_inv(x):
+        if inv_of is not None:
+            return inv_of(x)
+        return np.linalg.inv(diag_blocks(blocks_of(x)[0][None], mu)[0])
+
+    out = np.zeros((len(sites_e), n), dtype=np.complex128)
+    for i, x in enumerate(sites_e):
+        x = int(x)
+        if par[x] != 0:
+            raise ValueError(f"site {x} is not even")
+        hop_x = blocks_of(x)[1]
+        acc = np.zeros(n, dtype=np.complex128)
+        for d in range(8):
+            o = int(nb[x, d])
+            hop_o = blocks_of(o)[1]
+            w = sum(hop_o[dd] @ ve[half[nb[o, dd]]] for dd in range(8))
+            acc = acc + hop_x[d] @ (diag_inv(o) @ w)
+        out[i] = ve[half[x]] - diag_inv(x) @ acc
+    return out

@@ -15,6 +15,7 @@ COARSE_RESET_RECYCLE = 0x4
 COARSE_TIME_APPLY = 0x8
 COARSE_POLY_BF16 = 0x10
 COARSE_ODD_EVEN = 0x20
+COARSE_RECYCLE_FULL_CYCLE = 0x40
 
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "BREAKDOWN",
           -6: "NONFINITE", -7: "TIMEOUT", -8: "NOT_GAMMA5"}
@@ -23,7 +24,8 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED"
 EXPORTS = ["coarse_op_create", "coarse_op_update", "coarse_op_destroy", "coarse_apply", "coarse_apply_adjoint",
            "coarse_residual", "coarse_solve", "coarse_solve_adjoint", "coarse_solve_batched", "coarse_block_grad",
            "coarse_op_poly", "coarse_last_error", "coarse_version", "coarse_residual_noalloc",
-           "coarse_autotune_report", "coarse_schur_apply"]
+           "coarse_autotune_report", "coarse_schur_apply", "coarse_recycle_check",
+           "coarse_recycle_get", "coarse_autotune_set", "coarse_measure_fp64_fma"]
 
 
 class CoarseError(RuntimeError):
@@ -49,10 +51,15 @@ class SolveInfo(ctypes.Structure):
                 ("cycles", ctypes.c_int32), ("ir_steps", ctypes.c_int32), ("recycle_updates", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("apply_ms", ctypes.c_double), ("apply_count", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("apply_bytes", ctypes.c_double)]
+                ("apply_bytes", ctypes.c_double), ("apply_ms_prec", ctypes.c_double * 3),
+                ("apply_bytes_prec", ctypes.c_double * 3), ("apply_count_prec", ctypes.c_int32 * 3)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        out = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            out[f] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
 
 _lib = None
@@ -81,9 +88,13 @@ def lib() -> ctypes.CDLL:
     L.coarse_solve.argtypes = [vp, vp, vp, i32, P(SolveParams), P(SolveInfo), vp]
     L.coarse_solve_adjoint.argtypes = [vp, vp, vp, i32, P(SolveParams), P(SolveInfo), vp]
     L.coarse_solve_batched.argtypes = [P(vp), i32, P(vp), P(vp), P(i32), P(SolveParams), P(SolveInfo), vp]
-    L.coarse_block_grad.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.coarse_block_grad.argtypes = [vp, vp, vp, vp, vp, i32, vp]
     L.coarse_op_poly.argtypes = [vp, i32, P(dbl), i32, P(i32)]
+    L.coarse_recycle_check.argtypes = [vp, i32, i32, i32, P(dbl), vp]
+    L.coarse_recycle_get.argtypes = [vp, i32, i32, i32, vp, vp, i32, P(i32), vp]
     L.coarse_autotune_report.argtypes = [ctypes.c_char_p, ctypes.c_longlong]
+    L.coarse_autotune_set.argtypes = [ctypes.c_char_p, i32, i32, i32]
+    L.coarse_measure_fp64_fma.argtypes = [i32, P(dbl), vp]
     L.coarse_last_error.restype = ctypes.c_char_p
     L.coarse_version.restype = ctypes.c_char_p
     for name in EXPORTS:

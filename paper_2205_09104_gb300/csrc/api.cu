@@ -441,14 +441,65 @@ int coarse_solve_adjoint(coarse_op* op, const void* b, void* x, int nrhs, const 
 }
 
 int coarse_block_grad(const coarse_op* op, const void* lambda, const void* x, void* g_self, void* g_hop,
-                      void* stream) {
+                      int hop_dirs, void* stream) {
   if (!op) { set_error("op is NULL"); return COARSE_ERR_INVALID_ARG; }
   TRY(check_ptr(lambda, "lambda"));
   TRY(check_ptr(x, "x"));
   TRY(check_ptr(g_self, "g_self"));
   TRY(check_ptr(g_hop, "g_hop"));
-  return launch_block_grad((const double2*)lambda, (const double2*)x, op->nb, op->V, op->n, (double2*)g_self,
-                           (double2*)g_hop, (cudaStream_t)stream);
+  if (hop_dirs != 8 && hop_dirs != 4) {
+    set_error("hop_dirs = %d (8: canonical layout, 4: gamma5-compressed)", hop_dirs);
+    return COARSE_ERR_INVALID_ARG;
+  }
+  return launch_block_grad((const double2*)lambda, (const double2*)x, op->nb, op->V, op->n, hop_dirs,
+                           (double2*)g_self, (double2*)g_hop, (cudaStream_t)stream);
+}
+
+namespace {
+Solver* held_solver(coarse_op* op, int precision, int odd_even, int adjoint) {
+  const bool separate = adjoint && op->mu != 0.0;
+  return odd_even ? (separate ? op->eo_adj_solver[precision] : op->eo_solver[precision])
+                  : (separate ? op->adj_solver[precision] : op->solver[precision]);
+}
+}  // namespace
+
+int coarse_recycle_check(coarse_op* op, int precision, int odd_even, int adjoint, double* out_host, void* stream) {
+  if (!op) { set_error("op is NULL"); return COARSE_ERR_INVALID_ARG; }
+  TRY(check_ptr(out_host, "out_host"));
+  if (precision < 0 || precision > 2) { set_error("unknown precision %d", precision); return COARSE_ERR_INVALID_ARG; }
+  for (int i = 0; i < 4; ++i) out_host[i] = 0.0;
+  Solver* s = held_solver(op, precision, odd_even, adjoint);
+  if (!s) return COARSE_OK;
+  COARSE_CUDA(cudaSetDevice(op->device));
+  s->stream = (cudaStream_t)stream;
+  TRY(s->recycle_check(out_host));
+  return take_stencil_flag(op, (cudaStream_t)stream);
+}
+
+int coarse_recycle_get(coarse_op* op, int precision, int odd_even, int adjoint, void* u, void* c, int cap, int* k,
+                       void* stream) {
+  if (!op) { set_error("op is NULL"); return COARSE_ERR_INVALID_ARG; }
+  TRY(check_ptr(k, "k"));
+  if (precision < 0 || precision > 2) { set_error("unknown precision %d", precision); return COARSE_ERR_INVALID_ARG; }
+  *k = 0;
+  Solver* s = held_solver(op, precision, odd_even, adjoint);
+  if (!s || s->k_cur == 0 || !s->vecmem) return COARSE_OK;
+  if (cap < s->k_cur) {
+    set_error("cap = %d is below the %d recycle vectors held", cap, s->k_cur);
+    return COARSE_ERR_INVALID_ARG;
+  }
+  TRY(check_ptr(u, "u"));
+  TRY(check_ptr(c, "c"));
+  COARSE_CUDA(cudaSetDevice(op->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t col = (s->v64 ? sizeof(double2) : sizeof(float2)) * (size_t)s->N;
+  for (int i = 0; i < s->k_cur; ++i) {
+    COARSE_CUDA(cudaMemcpyAsync((char*)u + i * col, s->U[s->par][i], col, cudaMemcpyDeviceToDevice, st));
+    COARSE_CUDA(cudaMemcpyAsync((char*)c + i * col, s->C[s->par][i], col, cudaMemcpyDeviceToDevice, st));
+  }
+  COARSE_CUDA(cudaStreamSynchronize(st));
+  *k = s->k_cur;
+  return COARSE_OK;
 }
 
 int coarse_op_poly(const coarse_op* op, int precision, double* theta_host, int cap, int* d) {
@@ -456,6 +507,8 @@ int coarse_op_poly(const coarse_op* op, int precision, double* theta_host, int c
   TRY(check_ptr(d, "d"));
   if (precision < 0 || precision > 2) { set_error("unknown precision %d", precision); return COARSE_ERR_INVALID_ARG; }
   const Solver* s = op->solver[precision];
+  if (!(s && s->poly_ok && s->d > 0) && op->eo_solver[precision] && op->eo_solver[precision]->poly_ok)
+    s = op->eo_solver[precision];  // only odd-even solves have run: report their polynomial (of B^-1 D_c)
   *d = (s && s->poly_ok) ? s->d : 0;
   if (theta_host && s) {
     for (int i = 0; i < *d && i < cap; ++i) {

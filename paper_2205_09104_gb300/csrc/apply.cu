@@ -396,19 +396,13 @@ __global__ void __launch_bounds__(128) kb_residual64(BApply b, const double2* co
 // that accumulates (the polynomial chain) never runs twice; decisions are cached per process.
 template <class BT>
 int launch_tuned(int prec, int n, const ApplyArgs& a, cudaStream_t s) {
-  static int choice[3][32];  // [n/16 - 1][bucket]: -1 unknown
-  static bool init = false;
-  if (!init) {
-    for (auto& row : choice)
-      for (int& c : row) c = -1;
-    init = true;
-  }
   const int ni = n / 16 - 1, vb = std::min(tune_bucket(a.V), 31);
   if (ni < 0 || ni > 2) {
     set_error("coarse_apply: unsupported n = %d (nv must be 8, 16 or 24)", n);
     return COARSE_ERR_INVALID_ARG;
   }
-  if (choice[ni][vb] < 0) {
+  int choice = tune_fast_get(0, prec, ni, vb);
+  if (choice < 0) {
     char key[64];
     snprintf(key, sizeof(key), "apply/p%d/n%d/v%d", prec, n, vb);
     void* scratch = nullptr;
@@ -436,10 +430,10 @@ int launch_tuned(int prec, int n, const ApplyArgs& a, cudaStream_t s) {
       cudaFree(scratch);
     }
     if (rc != COARSE_OK) return rc;
-    if (cap != cudaStreamCaptureStatusNone) return c.a == 1 ? launch_t<BT, float2, float2>(n, a, s) : launch_tma<BT>(n, a, s);
-    choice[ni][vb] = c.a;
+    if (cap == cudaStreamCaptureStatusNone) tune_fast_put(0, prec, ni, vb, c.a);
+    choice = c.a;
   }
-  return choice[ni][vb] == 1 ? launch_t<BT, float2, float2>(n, a, s) : launch_tma<BT>(n, a, s);
+  return choice == 1 ? launch_t<BT, float2, float2>(n, a, s) : launch_tma<BT>(n, a, s);
 }
 
 int launch_apply(int prec, int n, const ApplyArgs& a, cudaStream_t s) {

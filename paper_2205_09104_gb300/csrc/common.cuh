@@ -192,7 +192,7 @@ int launch_ingest(const double2* self_b, const double2* hop_b, int gamma5_only, 
                   void* out64, void* out32, void* out16, cudaStream_t s);
 int launch_gamma5_defect(const double2* self_b, const double2* hop_b, int V, int n, const int* nb,
                          double* out2, cudaStream_t s);
-int launch_block_grad(const double2* lam, const double2* x, const int* nb, int V, int n, double2* g_self,
+int launch_block_grad(const double2* lam, const double2* x, const int* nb, int V, int n, int nhop, double2* g_self,
                       double2* g_hop, cudaStream_t s);
 
 }  // namespace coarse

@@ -1001,19 +1001,13 @@ int launch_eo_variant(int variant, int n, const EoArgs& a, cudaStream_t s) {
 // persistent layout (6); candidates run in plain mode into a scratch output.
 template <class BT, class VT, class AC>
 int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
-  static int choice[3][32];
-  static bool init = false;
-  if (!init) {
-    for (auto& row : choice)
-      for (int& c : row) c = -1;
-    init = true;
-  }
   const int ni = n / 16 - 1, vb = std::min(tune_bucket(a.V), 31);
   if (ni < 0 || ni > 2) {
     set_error("odd-even: unsupported n = %d", n);
     return COARSE_ERR_INVALID_ARG;
   }
-  if (choice[ni][vb] < 0) {
+  int choice = tune_fast_get(1, prec, ni, vb);
+  if (choice < 0) {
     char key[64];
     snprintf(key, sizeof(key), "eo/p%d/n%d/v%d", prec, n, vb);
     void* scratch = nullptr;
@@ -1050,10 +1044,10 @@ int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
       cudaFree(scratch);
     }
     if (rc != COARSE_OK) return rc;
-    if (cap != cudaStreamCaptureStatusNone) return launch_eo_variant<BT, VT, AC>(c.a, n, a, s);
-    choice[ni][vb] = c.a;
+    if (cap == cudaStreamCaptureStatusNone) tune_fast_put(1, prec, ni, vb, c.a);
+    choice = c.a;
   }
-  return launch_eo_variant<BT, VT, AC>(choice[ni][vb], n, a, s);
+  return launch_eo_variant<BT, VT, AC>(choice, n, a, s);
 }
 
 }  // namespace

@@ -75,22 +75,36 @@ __global__ void k_gamma5_defect(const double2* self_b, const double2* hop_b, int
 }
 
 // G_self[x][i][j] = -lambda_x[i] conj(x_x[j]);  G_hop[x][d][i][j] = -lambda_x[i] conj(x_{nb(x,d)}[j]).
+// nhop = 4 (gamma5-compressed input, backward hops derived as sigma3 F_{x-mu,mu}^H sigma3): the
+// backward hop of y + mu depends on F_{y,mu} antilinearly, so its gradient folds onto the forward
+// block as sigma3 G^H sigma3:  G4[y][mu][i][j] = -lambda_y[i] conj(x_{y+mu}[j])
+//                                                 - s_i s_j x_y[i] conj(lambda_{y+mu}[j]).
 // One thread per output entry; writes are coalesced along j.
-__global__ void k_block_grad(const double2* lam, const double2* xv, const int* nb, int V, int n, double2* g_self,
-                             double2* g_hop) {
+__global__ void k_block_grad(const double2* lam, const double2* xv, const int* nb, int V, int n, int nhop,
+                             double2* g_self, double2* g_hop) {
   const size_t nn = (size_t)n * n;
-  const size_t total = (size_t)V * 9 * nn;
+  const size_t nb_out = 1 + (size_t)nhop;
+  const size_t total = (size_t)V * nb_out * nn;
+  const int half = n / 2;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t x = e / (9 * nn);
-    const size_t r = e % (9 * nn);
+    const size_t x = e / (nb_out * nn);
+    const size_t r = e % (nb_out * nn);
     const int b = (int)(r / nn);
     const int i = (int)((r % nn) / n), j = (int)(r % n);
     const size_t src = (b == 0) ? x : (size_t)nb[x * 8 + (b - 1)];
     const double2 l = lam[x * n + i];
     const double2 v = xv[src * n + j];
-    const double2 g = make_double2(-(l.x * v.x + l.y * v.y), -(l.y * v.x - l.x * v.y));
+    double2 g = make_double2(-(l.x * v.x + l.y * v.y), -(l.y * v.x - l.x * v.y));
+    if (b > 0 && nhop == 4) {
+      // - s_i s_j x_y[i] conj(lambda_{y+mu}[j]), y = x, y + mu = src
+      const double2 xi = xv[x * n + i];
+      const double2 lj = lam[src * n + j];
+      const double sgn = ((i < half) == (j < half)) ? -1.0 : 1.0;
+      g.x += sgn * (xi.x * lj.x + xi.y * lj.y);
+      g.y += sgn * (xi.y * lj.x - xi.x * lj.y);
+    }
     if (b == 0) g_self[x * nn + (size_t)i * n + j] = g;
-    else g_hop[(x * 8 + (b - 1)) * nn + (size_t)i * n + j] = g;
+    else g_hop[(x * nhop + (b - 1)) * nn + (size_t)i * n + j] = g;
   }
 }
 
@@ -123,10 +137,10 @@ int launch_gamma5_defect(const double2* self_b, const double2* hop_b, int V, int
   return COARSE_OK;
 }
 
-int launch_block_grad(const double2* lam, const double2* x, const int* nb, int V, int n, double2* g_self,
+int launch_block_grad(const double2* lam, const double2* x, const int* nb, int V, int n, int nhop, double2* g_self,
                       double2* g_hop, cudaStream_t s) {
-  const size_t total = (size_t)V * 9 * n * n;
-  k_block_grad<<<grid_for(total), 256, 0, s>>>(lam, x, nb, V, n, g_self, g_hop);
+  const size_t total = (size_t)V * (1 + nhop) * n * n;
+  k_block_grad<<<grid_for(total), 256, 0, s>>>(lam, x, nb, V, n, nhop, g_self, g_hop);
   note_launch();
   COARSE_CUDA(cudaGetLastError());
   return COARSE_OK;

@@ -253,6 +253,7 @@ int Solver::apply(const void* x, void* y, int mode, void* accp, const double2* c
   const double nn = (double)op->n * op->n * (double)op->V, vn = (double)op->V * op->n;
   const double bytes = eo ? 9.0 * nn * esz[bprec] + 2.5 * vn * vsz : 5.0 * nn * esz[bprec] + 2.0 * (double)N * vsz;
   Timed tm{cur_tag, ev_pool.back(), nullptr, bytes};
+  tm.bprec = bprec;
   ev_pool.pop_back();
   tm.b = ev_pool.back();
   ev_pool.pop_back();
@@ -271,6 +272,9 @@ void Solver::harvest(int steps_done) {
         apply_ms += ms;
         apply_bytes += tm.bytes;
         ++apply_count;
+        prec_ms[tm.bprec] += ms;
+        prec_bytes[tm.bprec] += tm.bytes;
+        ++prec_count[tm.bprec];
       }
     }
     if (!tm.graph_owned) {
@@ -389,7 +393,9 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
     }
     const int steps = kc > 0 ? m - kc : m;
     void* const* tab = kc > 0 ? qtab[par] : vtab;
-    TRY(launch_cycle_init(st, kc, steps, norm2, target_abs, dn.g, stream));
+    // a cycle that is to yield the first recycle space runs all m steps (no least-squares stop)
+    const bool extract_full = full_first && kc == 0 && kdef > 0 && updates < ulimit;
+    TRY(launch_cycle_init(st, kc, steps, norm2, extract_full ? 0.0 : target_abs, dn.g, stream));
     TRY(launch_scale(v64, r, &st->inv_h, make_double2(1.0, 0.0), V[0], N, &st->stop, 0, stream));
     // Steps go out in chunks; the stop flag of chunk c-1 is read back (async copy +
     // event) while chunk c runs, so at most one chunk of gated launches follows a stop.
@@ -460,6 +466,38 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
     }
     if (cs.resid <= target_abs || (cs.status & ST_LUCKY)) return COARSE_OK;
   }
+  return COARSE_OK;
+}
+
+// Sec. 3.4: the recycle space satisfies A U_k = C_k and C_k^H C_k = I for the preconditioned
+// operator A = D q(D) it was built for.  Both relations are re-evaluated here from the held
+// vectors: one application of A per column (the polynomial chain included), one fused
+// reduction per column for C^H c_i.
+int Solver::recycle_check(double out[4]) {
+  out[0] = out[1] = 0.0;
+  out[2] = k_cur;
+  out[3] = updates;
+  if (k_cur == 0 || !vecmem) return COARSE_OK;
+  std::vector<double2> g(k_cur);
+  for (int c = 0; c < k_cur; ++c) {
+    TRY(opA(U[par][c], w, nullptr));
+    TRY(launch_axpy(v64, C[par][c], w, make_double2(-1.0, 0.0), N, nullptr, stream));
+    TRY(launch_norm2(v64, w, N, norm2, partial, counter, stream));
+    TRY(launch_norm2(v64, C[par][c], N, norm2 + 1, partial, counter, stream));
+    TRY(launch_multidot(v64, (const void* const*)qtab[par], k_cur, C[par][c], N, h1, nullptr, partial, counter,
+                        nullptr, stream));
+    double nn[2];
+    COARSE_CUDA(cudaMemcpyAsync(nn, norm2, sizeof(nn), cudaMemcpyDeviceToHost, stream));
+    COARSE_CUDA(cudaMemcpyAsync(g.data(), h1, sizeof(double2) * k_cur, cudaMemcpyDeviceToHost, stream));
+    COARSE_CUDA(cudaStreamSynchronize(stream));
+    const double rel = nn[1] > 0.0 ? sqrt(nn[0] / nn[1]) : INFINITY;
+    out[0] = fmax(out[0], rel);
+    for (int i = 0; i < k_cur; ++i) {
+      const double re = g[i].x - (i == c ? 1.0 : 0.0), im = g[i].y;
+      out[1] = fmax(out[1], sqrt(re * re + im * im));
+    }
+  }
+  harvest(1 << 30);
   return COARSE_OK;
 }
 
@@ -571,9 +609,14 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
   const long long mv0 = s->matvecs;
   const long long launches0 = launches_so_far();
   s->time_apply = (p->flags & COARSE_TIME_APPLY) != 0;
+  s->full_first = (p->flags & COARSE_RECYCLE_FULL_CYCLE) != 0;
   s->apply_ms = 0.0;
   s->apply_bytes = 0.0;
   s->apply_count = 0;
+  for (int q = 0; q < 3; ++q) {
+    s->prec_ms[q] = s->prec_bytes[q] = 0.0;
+    s->prec_count[q] = 0;
+  }
   if (!s->poly_ok || (p->flags & COARSE_REBUILD_POLY) || s->d_cap < dd || (dd > 0 && s->d == 0) ||
       (dd == 0 && s->d != 0)) {
     const double ts = now_ms();
@@ -650,6 +693,11 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
   inf.apply_ms = s->apply_ms;
   inf.apply_bytes = s->apply_bytes;
   inf.apply_count = (int)s->apply_count;
+  for (int q = 0; q < 3; ++q) {
+    inf.apply_ms_prec[q] = s->prec_ms[q];
+    inf.apply_bytes_prec[q] = s->prec_bytes[q];
+    inf.apply_count_prec[q] = (int)s->prec_count[q];
+  }
   inf.kernel_launches = (int)(launches_so_far() - launches0);
   inf.matvecs = (int)(s->matvecs - mv0);
   inf.recycle_updates = s->updates;

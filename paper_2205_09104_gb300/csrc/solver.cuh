@@ -62,14 +62,19 @@ struct Solver {
   // optional CUDA-event timing of the stencil launches (COARSE_TIME_APPLY)
   bool time_apply = false;
   int cur_tag = -1;                 // Arnoldi step of the applies being launched (-1: not gated)
-  struct Timed { int tag; cudaEvent_t a, b; double bytes; bool graph_owned = false; };
+  struct Timed { int tag; cudaEvent_t a, b; double bytes; bool graph_owned = false; int bprec = 0; };
   std::vector<Timed> timed;         // launched, not yet harvested
   std::vector<cudaEvent_t> ev_pool;
   double apply_ms = 0.0;
   double apply_bytes = 0.0;         // algorithmic bytes of the timed launches
   long long apply_count = 0;
+  double prec_ms[3] = {0.0, 0.0, 0.0};      // the same, split by the block precision of the launch
+  double prec_bytes[3] = {0.0, 0.0, 0.0};
+  long long prec_count[3] = {0, 0, 0};
   // blocks of the polynomial-chain applies (COARSE_POLY_BF16: BF16 while the Krylov operator keeps
   // `prec`); the recycle space belongs to the preconditioned operator of `rec_poly_prec`
+  // COARSE_RECYCLE_FULL_CYCLE: while no recycle space is held, cycles run all their steps
+  bool full_first = false;
   int poly_prec = COARSE_PREC_FP32;
   int rec_poly_prec = -1;
   // odd-even: the Krylov operator is S = 1 - D_ee^{-1} D_eo D_oo^{-1} D_oe on the even sites
@@ -101,6 +106,9 @@ struct Solver {
   int arnoldi_step(int j, int kc, void* const* tab);
   int build_poly(const double2* start64, uint64_t seed, int d);
   int inner(double target_abs, int max_cycles, int m, int kdef, int ulimit, InnerInfo* info);
+  // defects of the held recycle space: out[0] = max_i ||A u_i - c_i|| / ||c_i||,
+  // out[1] = max_ij |(C^H C - I)_ij|, out[2] = k held, out[3] = updates made (synchronises stream)
+  int recycle_check(double out[4]);
   void invalidate() {
     clear_graphs();
     poly_ok = false;

@@ -1,5 +1,6 @@
 // Launch autotuner (see tune.cuh) and the C entry point that reports its decisions.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -51,7 +52,61 @@ void append_cache(const std::string& key, const Entry& e) {
   fclose(f);
 }
 
+constexpr int kFastDevices = 64;
+std::atomic<int> g_fast[kFastDevices][2][3][3][32];
+std::once_flag g_fast_once;
+std::string g_model[kFastDevices];
+
+void fast_clear() {
+  for (auto& d : g_fast)
+    for (auto& f : d)
+      for (auto& p : f)
+        for (auto& n : p)
+          for (auto& v : n) v.store(-1, std::memory_order_relaxed);
+}
+
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (dev >= 0 && dev < kFastDevices) ? dev : -1;
+}
+
+// "@sm<major><minor>x<SMs>" of the current device (under g_mu)
+const std::string& model_suffix() {
+  static const std::string none;
+  const int dev = current_device();
+  if (dev < 0) return none;
+  if (g_model[dev].empty()) {
+    int maj = 0, mnr = 0, sms = 0;
+    cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    char buf[48];
+    snprintf(buf, sizeof(buf), "@sm%d%dx%d", maj, mnr, sms);
+    g_model[dev] = buf;
+  }
+  return g_model[dev];
+}
+
 }  // namespace
+
+int tune_fast_get(int family, int prec, int ni, int vb) {
+  std::call_once(g_fast_once, fast_clear);
+  const int dev = current_device();
+  if (dev < 0 || family < 0 || family > 1 || prec < 0 || prec > 2 || ni < 0 || ni > 2 || vb < 0 || vb > 31) return -1;
+  return g_fast[dev][family][prec][ni][vb].load(std::memory_order_acquire);
+}
+
+void tune_fast_put(int family, int prec, int ni, int vb, int choice) {
+  std::call_once(g_fast_once, fast_clear);
+  const int dev = current_device();
+  if (dev < 0 || family < 0 || family > 1 || prec < 0 || prec > 2 || ni < 0 || ni > 2 || vb < 0 || vb > 31) return;
+  g_fast[dev][family][prec][ni][vb].store(choice, std::memory_order_release);
+}
 
 int tune_bucket(long long v) {
   int b = 0;
@@ -61,10 +116,13 @@ int tune_bucket(long long v) {
 
 int tune_pick(const std::string& key, const std::vector<TuneChoice>& cands,
               const std::function<int(const TuneChoice&)>& run, cudaStream_t s, TuneChoice* out) {
+  std::string mkey;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_cache();
-    auto it = g_table.find(key);
+    mkey = key + model_suffix();
+    auto it = g_table.find(mkey);
+    if (it == g_table.end()) it = g_table.find(key);  // a model-independent entry (cache file, set)
     if (it != g_table.end()) {
       *out = it->second.choice;
       return COARSE_OK;
@@ -115,8 +173,8 @@ int tune_pick(const std::string& key, const std::vector<TuneChoice>& cands,
   best.tried = tried.str();
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_table[key] = best;
-    append_cache(key, best);
+    g_table[mkey] = best;
+    append_cache(mkey, best);
   }
   *out = best.choice;
   return COARSE_OK;
@@ -143,5 +201,40 @@ extern "C" int coarse_autotune_report(char* buf, long long len) {
   const size_t n = std::min<size_t>(s.size(), (size_t)len - 1);
   memcpy(buf, s.data(), n);
   buf[n] = '\0';
+  return COARSE_OK;
+}
+
+// Fixes the decision for `key` (a key as coarse_autotune_report prints it, with or without the
+// model suffix) for every later launch in this process.
+extern "C" int coarse_autotune_set(const char* key, int a, int b, int c) {
+  using namespace coarse;
+  if (!key || !*key) {
+    set_error("coarse_autotune_set: empty key");
+    return COARSE_ERR_INVALID_ARG;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_cache();
+    const std::string k(key);
+    if (a >= 0) {
+      Entry e;
+      e.choice = TuneChoice{a, b, c};
+      e.tried = "set";
+      g_table[k] = e;
+    } else {
+      g_table.erase(k);  // a < 0: forget the decision; the next launch times the candidates again
+    }
+    // a plain key overrides (or, with a < 0, forgets) every model-specific decision of that shape
+    if (k.find('@') == std::string::npos) {
+      for (auto it = g_table.begin(); it != g_table.end();) {
+        if (it->first.size() > k.size() && it->first.compare(0, k.size(), k) == 0 && it->first[k.size()] == '@')
+          it = g_table.erase(it);
+        else
+          ++it;
+      }
+    }
+  }
+  std::call_once(g_fast_once, fast_clear);
+  fast_clear();
   return COARSE_OK;
 }

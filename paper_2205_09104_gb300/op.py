@@ -133,13 +133,36 @@ class CoarseOp:
         check(rc, allow_not_converged)
         return x, [i.as_dict() for i in infos]
 
-    def block_grad(self, lam: torch.Tensor, x: torch.Tensor, stream=None):
+    def block_grad(self, lam: torch.Tensor, x: torch.Tensor, hop_dirs: int = 8, stream=None):
+        """Block gradients -lambda_x x_y^H: g_self [V, n, n] and g_hop [V, hop_dirs, n, n]
+        (hop_dirs = 4: with respect to the forward blocks of a gamma5-compressed input)."""
         lam, _ = self._vec(lam, torch.complex128)
         x, _ = self._vec(x, torch.complex128)
         gs = torch.empty((self.V, self.n, self.n), dtype=torch.complex128, device=lam.device)
-        gh = torch.empty((self.V, 8, self.n, self.n), dtype=torch.complex128, device=lam.device)
-        check(lib().coarse_block_grad(self.handle, _ptr(lam), _ptr(x), _ptr(gs), _ptr(gh), _stream(stream)))
+        gh = torch.empty((self.V, hop_dirs, self.n, self.n), dtype=torch.complex128, device=lam.device)
+        check(lib().coarse_block_grad(self.handle, _ptr(lam), _ptr(x), _ptr(gs), _ptr(gh), hop_dirs, _stream(stream)))
         return gs, gh
+
+    def recycle_check(self, precision: int, odd_even: bool = False, adjoint: bool = False, stream=None) -> dict:
+        """Defects of the held GCRO-DR recycle space: ||A u_i - c_i|| / ||c_i|| (max over i),
+        max |C^H C - I|, the columns held and the updates made."""
+        out = (ctypes.c_double * 4)()
+        check(lib().coarse_recycle_check(self.handle, precision, int(odd_even), int(adjoint), out, _stream(stream)))
+        return {"au_minus_c": out[0], "chc_minus_i": out[1], "k": int(out[2]), "updates": int(out[3])}
+
+    def recycle_get(self, precision: int, odd_even: bool = False, adjoint: bool = False, cap: int = 64,
+                    stream=None):
+        """The held recycle space (U_k, C_k) as two [k, N] tensors (None if none is held)."""
+        dt = _PREC_DT[precision]
+        N = self.V * self.n // (2 if odd_even else 1)
+        u = torch.empty((cap, N), dtype=dt, device=self.device)
+        c = torch.empty_like(u)
+        k = ctypes.c_int()
+        check(lib().coarse_recycle_get(self.handle, precision, int(odd_even), int(adjoint), _ptr(u), _ptr(c), cap,
+                                       ctypes.byref(k), _stream(stream)))
+        if k.value == 0:
+            return None
+        return u[: k.value], c[: k.value]
 
     def poly(self, precision: int):
         buf = (ctypes.c_double * 64)()
@@ -172,6 +195,7 @@ class CoarseSolve(torch.autograd.Function):
     def forward(ctx, b, self_blocks, hop_blocks, op: CoarseOp, params: SolveParams):
         x, info = op.solve(b.detach(), params=params)
         ctx.op, ctx.params = op, params
+        ctx.hop_dirs = hop_blocks.shape[1]   # 4: gamma5-compressed input (forward hops only)
         ctx.save_for_backward(x)
         return x
 
@@ -181,7 +205,7 @@ class CoarseSolve(torch.autograd.Function):
         lam, _ = ctx.op.solve(gx.contiguous(), params=ctx.params, adjoint=True)
         gs = gh = None
         if ctx.needs_input_grad[1] or ctx.needs_input_grad[2]:
-            gs, gh = ctx.op.block_grad(lam, x)
+            gs, gh = ctx.op.block_grad(lam, x, hop_dirs=ctx.hop_dirs)
         return lam, gs, gh, None, None
 
 
@@ -190,3 +214,15 @@ def autotune_report() -> str:
     buf = ctypes.create_string_buffer(1 << 16)
     check(lib().coarse_autotune_report(buf, len(buf)))
     return buf.value.decode()
+
+
+def autotune_set(key: str, a: int, b: int = 0, c: int = 0) -> None:
+    """Fix the launch configuration of one kernel family and shape (coarse_autotune_set)."""
+    check(lib().coarse_autotune_set(key.encode(), a, b, c))
+
+
+def measure_fp64_fma(iters: int = 20000, stream=None) -> float:
+    """FP64 FMA throughput of the current device in TFLOP/s (coarse_measure_fp64_fma)."""
+    out = ctypes.c_double()
+    check(lib().coarse_measure_fp64_fma(iters, ctypes.byref(out), _stream(stream)))
+    return out.value

@@ -8,7 +8,7 @@ import numpy as np
 import torch
 
 sys.path.insert(0, __file__.rsplit("/", 1)[0])
-from gpu_helpers import make_op, rel, rhs  # noqa: E402
+from gpu_helpers import check_schur_entrywise, make_op, rel, rhs  # noqa: E402
 from oracle import coarse as ocoarse  # noqa: E402
 from oracle import oddeven as ooe  # noqa: E402
 
@@ -31,6 +31,8 @@ def main(nv, fdims, mu):
         dt = torch.complex128 if prec == 0 else torch.complex64
         y = dev.schur(torch.from_numpy(x).to("cuda", dt), precision=prec).cpu().numpy()
         assert rel(y, ref) <= TOL[prec], (prec, rel(y, ref))
+        check_schur_entrywise(y, torch.from_numpy(x).to(dt).numpy(), op.self_blocks.numpy(), op.hop_blocks.numpy(),
+                              op.dims, prec, mu, f"layout worker {fdims}")
     from paper_2205_09104_gb300 import COARSE_ODD_EVEN, COARSE_POLY_BF16, COARSE_ZERO_GUESS, solve_params
     sb, hb = op.self_blocks.numpy(), op.hop_blocks.numpy()
     b = rhs((542, nv), 1, 2 * N2)[0]

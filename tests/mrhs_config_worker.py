@@ -7,7 +7,7 @@ import numpy as np
 import torch
 
 sys.path.insert(0, __file__.rsplit("/", 1)[0])
-from gpu_helpers import make_op, rel, rhs  # noqa: E402
+from gpu_helpers import abs_apply, assert_entrywise, make_op, rel, rhs, stencil_factor  # noqa: E402
 from oracle import coarse as ocoarse  # noqa: E402
 from oracle.lattice import neighbours  # noqa: E402
 
@@ -43,6 +43,9 @@ def main(nv, fine_dims_list, nrhs_list):
                 ref = ocoarse.apply(sr, hr, op.dims, Xr[c], 0.0) + 1j * 0.02 * s3v * X32[c]
                 err = rel(Y[c], ref)
                 assert err <= 2e-5, (fdims, nrhs, c, err)
+                mag = abs_apply(sr, hr, op.dims, Xr[c]) + 0.02 * np.abs(X32[c])
+                assert_entrywise(Y[c], ref, stencil_factor(2, op.n, rounded_operands=True) * mag,
+                                 f"{fdims} nrhs={nrhs} column {c}")
         dev.close()
     print(autotune_report())
     print("ok")

@@ -109,3 +109,77 @@ def test_gradient_with_odd_even_forward():
     assert rel(S.grad.cpu().numpy(), rs) <= 1e-6
     assert rel(H.grad.cpu().numpy(), rh) <= 1e-6
     dev.close()
+
+
+@pytest.mark.parametrize("hop_dirs", [8, 4])
+def test_block_grad_kernel_entrywise(hop_dirs):
+    """coarse_block_grad on given lambda and x, every entry against the oracle's -lambda_x x_y^H
+    (hop_dirs = 4: plus the backward-hop gradient of x + mu folded onto F_{x,mu} as
+    sigma3 G^H sigma3) within 8 u of the products' magnitudes."""
+    from gpu_helpers import U64, assert_entrywise, to_cuda
+    from oracle.lattice import neighbours
+    op = make_op((702, 0), (6, 4, 4, 6), 16, m0=-0.4)
+    n, V = op.n, op.volume
+    dev = to_cuda(op, precisions=())
+    g = np.random.default_rng(5)
+    lam = g.standard_normal(V * n) + 1j * g.standard_normal(V * n)
+    x = g.standard_normal(V * n) + 1j * g.standard_normal(V * n)
+    gs, gh = dev.block_grad(torch.from_numpy(lam).cuda(), torch.from_numpy(x).cuda(), hop_dirs=hop_dirs)
+    gs, gh = gs.cpu().numpy(), gh.cpu().numpy()
+    rs, rh = ograd.block_gradient(lam, x, op.dims, n)
+    nb = neighbours(op.dims)
+    L, X = np.abs(lam.reshape(V, n)), np.abs(x.reshape(V, n))
+    ms = L[:, :, None] * X[:, None, :]
+    mh = L[:, None, :, None] * X[nb][:, :, None, :]
+    assert_entrywise(gs, rs, 8 * U64 * ms, "g_self")
+    if hop_dirs == 8:
+        assert_entrywise(gh, rh, 8 * U64 * mh, "g_hop")
+        return
+    s3 = ocoarse.sigma3(n // 2)
+    want = rh[:, :4].copy()
+    mag = mh[:, :4].copy()
+    for mu in range(4):
+        back = rh[nb[:, mu], 4 + mu]          # gradient of D[x + mu, x] = sigma3 F_{x,mu}^H sigma3
+        want[:, mu] += s3[None, :, None] * np.conj(np.transpose(back, (0, 2, 1))) * s3[None, None, :]
+        mag[:, mu] += np.transpose(mh[nb[:, mu], 4 + mu], (0, 2, 1))
+    assert_entrywise(gh, want, 8 * U64 * mag, "g_hop folded")
+
+
+def test_gradient_gamma5_compressed_input_vs_fd():
+    """CoarseSolve on a gamma5-compressed operator (hop blocks [V, 4, n, n], backward hops
+    derived): the gradient with respect to the forward blocks against central finite
+    differences of the oracle's loss with the backward hops rebuilt from the perturbed block."""
+    from paper_2205_09104_gb300 import CoarseOp, CoarseSolve, solve_params
+    from oracle.lattice import neighbours
+    op = make_op((703, 0), (6, 4, 4, 6), 8, m0=-0.4)
+    n, V = op.n, op.volume
+    N = n * V
+    c, b, ent = draws.grad_draws((703, 1), N, V, n, 16)
+    s, h = op.self_blocks.numpy(), op.hop_blocks.numpy()
+    S = op.self_blocks.cuda().requires_grad_()
+    H4 = op.hop_blocks[:, :4].contiguous().cuda().requires_grad_()
+    dev = CoarseOp(S.detach(), H4.detach(), op.dims, op.nv, precisions=(1,), assume_gamma5=True)
+    p = solve_params(m=30, tol=1e-12, precision=1, poly_degree=4, defl_k=8, inner_tol=1e-5)
+    bt = torch.from_numpy(b).cuda().requires_grad_()
+    x = CoarseSolve.apply(bt, S, H4, dev, p)
+    (torch.from_numpy(c).cuda().conj() * x).sum().real.backward()
+    assert H4.grad.shape == H4.shape
+    gh = H4.grad.cpu().numpy()
+    nb = neighbours(op.dims)
+    s3 = ocoarse.sigma3(n // 2)
+
+    def loss_with(site, mu, i, j, delta):
+        hp = h.copy()
+        hp[site, mu, i, j] += delta
+        y = nb[site, mu]
+        hp[y, 4 + mu] = s3[:, None] * np.conj(hp[site, mu].T) * s3[None, :]
+        return ograd.loss(s, hp, op.dims, b, c)
+
+    scale = np.abs(gh).max()
+    for k, (site, blk, i, j) in enumerate(ent):
+        mu = int(blk) % 4
+        eps = 1e-6
+        fd = ((loss_with(site, mu, i, j, eps) - loss_with(site, mu, i, j, -eps))
+              + 1j * (loss_with(site, mu, i, j, 1j * eps) - loss_with(site, mu, i, j, -1j * eps))) / (2 * eps)
+        assert abs(gh[site, mu, i, j] - fd) <= 1e-6 * max(abs(fd), 1e-2 * scale), (k, gh[site, mu, i, j], fd)
+    dev.close()

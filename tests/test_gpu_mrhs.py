@@ -6,7 +6,8 @@ Two bars per column:
   * against the oracle applied, in FP64, to the BF16-rounded forward blocks (backward hops rebuilt
     from them by sigma3 F^H sigma3, as the kernel does) and the BF16-rounded vector, plus the
     twisted-mass term i mu sigma3 x taken from the unrounded (complex64) vector as the kernel's
-    epilogue does: 2e-5 relative.  Only the FP32 accumulation differs there (9n-term sums at 2^-24), so an index,
+    epilogue does: 2e-5 relative, and entry by entry (9n + 5) 2^-24 of (|D_c| |x|)_i on those
+    operands.  Only the FP32 accumulation differs there (9n-term sums at 2^-24), so an index,
     sign or transposition error anywhere in the fragment layout is an O(1) difference.
 Column counts cover one partial tile (2, 5), full passes (12) and a second pass (13, 24).
 """
@@ -14,7 +15,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import make_op, rel, rhs
+from gpu_helpers import abs_apply, assert_entrywise, make_op, rel, rhs, stencil_factor
 from oracle import coarse as ocoarse
 from oracle.lattice import neighbours
 
@@ -67,6 +68,9 @@ def test_mrhs_matches_oracle(ops, nv, nrhs, mu, adjoint):
         assert rel(Y[c], exact) <= 1e-2, (c, rel(Y[c], exact))
         rounded = f(sr, hr, op.dims, Xr[c], 0.0) + (-1j if adjoint else 1j) * mu * s3 * X32[c]
         assert rel(Y[c], rounded) <= 2e-5, (c, rel(Y[c], rounded))
+        mag = abs_apply(sr, hr, op.dims, Xr[c], 0.0, adjoint=adjoint) + mu * np.abs(X32[c])
+        assert_entrywise(Y[c], rounded, stencil_factor(2, op.n, rounded_operands=True) * mag,
+                         f"nv={nv} nrhs={nrhs} mu={mu} adjoint={adjoint} column {c}")
     dev.close()
 
 

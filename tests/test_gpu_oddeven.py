@@ -9,7 +9,7 @@ import pytest
 import scipy.sparse.linalg as spla
 import torch
 
-from gpu_helpers import make_op, rel, rhs
+from gpu_helpers import check_schur_entrywise, make_op, rel, rhs
 from oracle import coarse as ocoarse
 from oracle import oddeven as ooe
 
@@ -42,6 +42,8 @@ def test_schur_apply_matches_oracle(ops, nv, prec, mu):
     y = dev.schur(torch.from_numpy(x).to("cuda", dt), precision=prec).cpu().numpy()
     ref = ooe.schur_apply(op.self_blocks.numpy(), op.hop_blocks.numpy(), op.dims, x, mu)
     assert rel(y, ref) <= TOL[prec], rel(y, ref)
+    xin = torch.from_numpy(x).to(dt).numpy()
+    check_schur_entrywise(y, xin, op.self_blocks.numpy(), op.hop_blocks.numpy(), op.dims, prec, mu, f"nv={nv} mu={mu}")
     dev.close()
 
 

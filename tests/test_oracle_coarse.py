@@ -121,3 +121,18 @@ def test_generator_matches_oracle(which, request):
     assert np.abs(op.self_blocks.numpy() - st["self"]).max() / scale < 1e-12
     assert np.abs(op.hop_blocks.numpy() - st["hop"]).max() / scale < 1e-12
     assert op.dims == st["cdims"]
+
+
+def test_apply_at_equals_whole_lattice_apply(ragged_setup):
+    """The per-site evaluation (used on sampled sites of lattices too large for the host) is the
+    same stencil as the whole-lattice apply, which the assembled matrix pins."""
+    st = ragged_setup
+    s, h, dims = st["self"], st["hop"], st["cdims"]
+    from synthetic import draws
+    N = s.shape[0] * s.shape[1]
+    v = draws.rhs((*st["key"], 90), 1, N)[0]
+    sites = np.arange(s.shape[0])
+    for mu in (0.0, 0.05):
+        full = coarse.apply(s, h, dims, v, mu).reshape(s.shape[0], -1)
+        at = coarse.apply_at(lambda x: (s[x], h[x]), dims, v, sites, mu)
+        assert np.abs(at - full).max() <= 1e-13 * np.abs(full).max()

@@ -92,3 +92,19 @@ def test_block_inverses(op):
     blk = oe.diag_blocks(op.s, 0.05)
     eye = np.eye(op.n)
     assert max(np.linalg.norm(blk[x] @ inv[x] - eye) for x in range(op.volume)) <= 1e-12
+
+
+def test_schur_at_equals_whole_lattice_schur():
+    """The per-site evaluation of S (for sampled sites of large lattices) equals the factored
+    whole-lattice S, which the dense Schur algebra pins."""
+    from synthetic.coarse_op import build_coarse_operator
+    from synthetic import draws
+    op = build_coarse_operator((905, 0), (8, 4, 4, 8), 4, -0.4, 1.0)
+    s, h = op.self_blocks.numpy(), op.hop_blocks.numpy()
+    N2 = s.shape[0] * s.shape[1] // 2
+    v = draws.rhs((905, 1), 1, N2)[0]
+    ev = oe.sites(op.dims, 0)
+    for mu in (0.0, 0.05):
+        full = oe.schur_apply(s, h, op.dims, v, mu).reshape(len(ev), -1)
+        at = oe.schur_at(lambda x: (s[x], h[x]), op.dims, v, ev, mu)
+        assert np.abs(at - full).max() <= 1e-12 * np.abs(full).max()
