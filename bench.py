@@ -324,12 +324,14 @@ def run_gb300(args):
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for i in range(args.steps):
             _, inf = cop.solve(B[args.warmup + i], X[args.warmup + i], params=p)
             infos.append(inf[0])
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         barrier()
     ms = replicas.max_over_ranks(e0.elapsed_time(e1), dev)
     value = replicas.job_rate(args.steps, world, ms)
@@ -582,6 +584,7 @@ APPLY_CASES = {
     "wilson8": ((16, 16, 16, 16), 16, -0.42, 0.0, "wilson-clover coarse 8^4, n=32"),
     "tm16": ((32, 32, 32, 32), 24, -0.42, 3e-3, "twisted mass coarse 16^4, n=48, mu=3e-3"),
     "tm12": ((24, 24, 24, 24), 24, -0.42, 3e-3, "twisted mass coarse 12^4, n=48, mu=3e-3 (profiling size)"),
+    "tm8": ((16, 16, 16, 16), 24, -0.42, 3e-3, "twisted mass coarse 8^4, n=48, mu=3e-3 (profiling size)"),
 }
 
 

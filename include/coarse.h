@@ -195,6 +195,17 @@ int coarse_residual_noalloc(const coarse_op* op, const void* b, const void* x, v
  * when the system would converge sooner; the extra steps only refine that cycle's correction.
  * Meant for a setup solve; later solves reuse the space without the flag. */
 #define COARSE_RECYCLE_FULL_CYCLE 0x40u
+/* Latency-1 pipelined Arnoldi (Sec. 3.5, Alg. "pipe1fgmres" / "pipe1gcrodr", shifts sigma = 0):
+ * the basis carries v^a_i = A v_i, so that the stencil of step i (A v^a_{i-1}) and the step's one
+ * fused reduction ([C, V]^H v^a_{i-1} and ||v^a_{i-1}||^2) are independent and run concurrently on
+ * two streams; h_{i,i-1} = sqrt(||v^a||^2 - sum |h|^2 - sum |b|^2) replaces the second reduction,
+ * and both recurrences (v, v^a) share the coefficients.  A negative value (loss of orthogonality)
+ * is a breakdown: the cycle ends with the steps before it, the next cycle restarts from the
+ * residual (coarse_solve_info.breakdowns counts them).  Every cycle of plain (pp-)GMRES is
+ * pipelined; GCRO-DR's first cycle, without a recycle space, stays the classical GMRES cycle, and
+ * each pipelined GCRO-DR cycle needs the k products A c_j of the recycle vectors (computed once per
+ * recycle space).  Costs m + 1 + 2k extra vectors of storage. */
+#define COARSE_PIPELINED 0x80u
 
 typedef struct {
   int32_t m;               /* restart length of GMRES / GCRO-DR (Sec. 3.1), 2 .. 64 */
@@ -208,7 +219,7 @@ typedef struct {
   int32_t max_ir;          /* FP64 iterative-refinement steps allowed */
   uint32_t flags;          /* COARSE_ZERO_GUESS | COARSE_REBUILD_POLY | COARSE_RESET_RECYCLE |
                               COARSE_TIME_APPLY | COARSE_POLY_BF16 | COARSE_ODD_EVEN |
-                              COARSE_RECYCLE_FULL_CYCLE */
+                              COARSE_RECYCLE_FULL_CYCLE | COARSE_PIPELINED */
   uint64_t seed;           /* seeds the polynomial start vector when poly_start is NULL */
   const void* poly_start;  /* optional device complex128 [V][n]: start vector of the polynomial's Arnoldi */
 } coarse_solve_params;
@@ -232,6 +243,7 @@ typedef struct {
   double apply_ms_prec[3];    /* apply_ms split by the block precision of the launch (coarse_precision) */
   double apply_bytes_prec[3]; /* apply_bytes, split the same way */
   int32_t apply_count_prec[3];/* apply_count, split the same way */
+  int32_t breakdowns;         /* pipelined cycles ended by a negative h^2 (COARSE_PIPELINED) */
 } coarse_solve_info;
 
 /*
@@ -364,6 +376,22 @@ int coarse_recycle_get(coarse_op* op, int precision, int odd_even, int adjoint, 
  * The paper has no counterpart.
  */
 int coarse_measure_fp64_fma(int iters, double* tflops_host, void* stream);
+
+/*
+ * coarse_recycle_set -- installs a recycle space (U_k, C_k; Sec. 3.4) for the system named as in
+ * coarse_recycle_check, e.g. one saved with coarse_recycle_get, so that later solves deflate
+ * with it from their first cycle.  The space must belong to the right-preconditioned operator
+ * A = D q(D) that the solver currently holds (same polynomial) and satisfy A U_k = C_k,
+ * C_k^H C_k = I; nothing checks this (coarse_recycle_check measures it afterwards).
+ * u, c    : device [k][N] as for coarse_recycle_get (copied; the caller keeps ownership).
+ * k       : columns; 0 drops the recycle space.
+ * updates : the solver's count of updates made, compared with recycle_updates of later solves
+ *           (>= recycle_updates keeps the space frozen).
+ * The handle must already hold a solver of that system created with defl_k >= k (one solve with
+ * those parameters); COARSE_ERR_INVALID_ARG otherwise.  Synchronises `stream`.
+ */
+int coarse_recycle_set(coarse_op* op, int precision, int odd_even, int adjoint, const void* u, const void* c, int k,
+                       int updates, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* coarse_last_error(void);

@@ -14,7 +14,7 @@ import os
 
 from . import _abi
 from ._abi import (COARSE_ASSUME_GAMMA5, COARSE_ODD_EVEN, COARSE_POLY_BF16, COARSE_REBUILD_POLY,
-                   COARSE_RECYCLE_FULL_CYCLE, COARSE_RESET_RECYCLE, COARSE_TIME_APPLY, COARSE_ZERO_GUESS, PREC_BF16,
+                   COARSE_PIPELINED, COARSE_RECYCLE_FULL_CYCLE, COARSE_RESET_RECYCLE, COARSE_TIME_APPLY, COARSE_ZERO_GUESS, PREC_BF16,
                    PREC_FP32, PREC_FP64, CoarseError, SolveInfo, SolveParams, lib, lib_path)
 from .op import (CoarseOp, CoarseSolve, autotune_report, autotune_set, measure_fp64_fma, solve_batched,
                  solve_params)
@@ -22,7 +22,7 @@ from .op import (CoarseOp, CoarseSolve, autotune_report, autotune_set, measure_f
 __all__ = ["CoarseOp", "CoarseSolve", "autotune_report", "autotune_set", "measure_fp64_fma", "solve_batched", "solve_params", "SolveParams", "SolveInfo", "CoarseError", "lib", "lib_path",
            "PREC_FP64", "PREC_FP32", "PREC_BF16", "COARSE_ZERO_GUESS", "COARSE_REBUILD_POLY",
            "COARSE_RESET_RECYCLE", "COARSE_ASSUME_GAMMA5", "COARSE_TIME_APPLY", "COARSE_POLY_BF16", "COARSE_ODD_EVEN",
-           "COARSE_RECYCLE_FULL_CYCLE", "build"]
+           "COARSE_RECYCLE_FULL_CYCLE", "COARSE_PIPELINED", "build"]
 
 
 def build(force: bool = False) -> str:

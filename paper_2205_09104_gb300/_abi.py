@@ -16,6 +16,7 @@ COARSE_TIME_APPLY = 0x8
 COARSE_POLY_BF16 = 0x10
 COARSE_ODD_EVEN = 0x20
 COARSE_RECYCLE_FULL_CYCLE = 0x40
+COARSE_PIPELINED = 0x80
 
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "BREAKDOWN",
           -6: "NONFINITE", -7: "TIMEOUT", -8: "NOT_GAMMA5"}
@@ -25,7 +26,7 @@ EXPORTS = ["coarse_op_create", "coarse_op_update", "coarse_op_destroy", "coarse_
            "coarse_residual", "coarse_solve", "coarse_solve_adjoint", "coarse_solve_batched", "coarse_block_grad",
            "coarse_op_poly", "coarse_last_error", "coarse_version", "coarse_residual_noalloc",
            "coarse_autotune_report", "coarse_schur_apply", "coarse_recycle_check",
-           "coarse_recycle_get", "coarse_autotune_set", "coarse_measure_fp64_fma"]
+           "coarse_recycle_get", "coarse_autotune_set", "coarse_measure_fp64_fma", "coarse_recycle_set"]
 
 
 class CoarseError(RuntimeError):
@@ -52,7 +53,8 @@ class SolveInfo(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("apply_ms", ctypes.c_double), ("apply_count", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("apply_bytes", ctypes.c_double), ("apply_ms_prec", ctypes.c_double * 3),
-                ("apply_bytes_prec", ctypes.c_double * 3), ("apply_count_prec", ctypes.c_int32 * 3)]
+                ("apply_bytes_prec", ctypes.c_double * 3), ("apply_count_prec", ctypes.c_int32 * 3),
+                ("breakdowns", ctypes.c_int32)]
 
     def as_dict(self):
         out = {}
@@ -92,6 +94,7 @@ def lib() -> ctypes.CDLL:
     L.coarse_op_poly.argtypes = [vp, i32, P(dbl), i32, P(i32)]
     L.coarse_recycle_check.argtypes = [vp, i32, i32, i32, P(dbl), vp]
     L.coarse_recycle_get.argtypes = [vp, i32, i32, i32, vp, vp, i32, P(i32), vp]
+    L.coarse_recycle_set.argtypes = [vp, i32, i32, i32, vp, vp, i32, i32, vp]
     L.coarse_autotune_report.argtypes = [ctypes.c_char_p, ctypes.c_longlong]
     L.coarse_autotune_set.argtypes = [ctypes.c_char_p, i32, i32, i32]
     L.coarse_measure_fp64_fma.argtypes = [i32, P(dbl), vp]

@@ -502,6 +502,35 @@ int coarse_recycle_get(coarse_op* op, int precision, int odd_even, int adjoint, 
   return COARSE_OK;
 }
 
+int coarse_recycle_set(coarse_op* op, int precision, int odd_even, int adjoint, const void* u, const void* c, int k,
+                       int updates, void* stream) {
+  if (!op) { set_error("op is NULL"); return COARSE_ERR_INVALID_ARG; }
+  if (precision < 0 || precision > 2) { set_error("unknown precision %d", precision); return COARSE_ERR_INVALID_ARG; }
+  Solver* s = held_solver(op, precision, odd_even, adjoint);
+  if (!s || !s->vecmem || s->k_cap < k || k < 0) {
+    set_error("coarse_recycle_set: no solver of this system with room for k = %d recycle vectors (solve once "
+              "with defl_k = %d first)", k, k);
+    return COARSE_ERR_INVALID_ARG;
+  }
+  if (k > 0) {
+    TRY(check_ptr(u, "u"));
+    TRY(check_ptr(c, "c"));
+  }
+  COARSE_CUDA(cudaSetDevice(op->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t col = (s->v64 ? sizeof(double2) : sizeof(float2)) * (size_t)s->N;
+  for (int i = 0; i < k; ++i) {
+    COARSE_CUDA(cudaMemcpyAsync(s->U[s->par][i], (const char*)u + i * col, col, cudaMemcpyDeviceToDevice, st));
+    COARSE_CUDA(cudaMemcpyAsync(s->C[s->par][i], (const char*)c + i * col, col, cudaMemcpyDeviceToDevice, st));
+  }
+  COARSE_CUDA(cudaStreamSynchronize(st));
+  s->k_cur = k;
+  s->updates = updates < 0 ? 0 : updates;
+  s->rec_poly_prec = s->poly_prec;
+  s->vc_par = -1;
+  return COARSE_OK;
+}
+
 int coarse_op_poly(const coarse_op* op, int precision, double* theta_host, int cap, int* d) {
   if (!op) { set_error("op is NULL"); return COARSE_ERR_INVALID_ARG; }
   TRY(check_ptr(d, "d"));

@@ -55,12 +55,12 @@ __device__ void finalize_warp(CycleState* st, const double2* h1, const double2* 
   const double2 gj = d.g[j];
   double hn2 = 0.0;
   for (int i = lane; i < k; i += 32) {
-    const double2 b = add(h1[i], h2[i]);
+    const double2 b = h2 ? add(h1[i], h2[i]) : h1[i];
     d.B[j * d.ldb + i] = b;
     hn2 += abs2(b);
   }
   for (int i = lane; i <= j; i += 32) {
-    const double2 h = add(h1[k + i], h2[k + i]);
+    const double2 h = h2 ? add(h1[k + i], h2[k + i]) : h1[k + i];
     d.H[j * ldh + i] = h;
     col[i] = h;
     hn2 += abs2(h);
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(32) k_recycle(CycleState* st, Dense d, const d
     Sbot[r * k + c] = SW[c * ldsw + k + r];
   }
   tm.sync();
-  int rc = harmonic_matrix(tm, k, j, d.cs, d.sn, d.R, d.ldh, d.B, Stop, Sbot, M, LD);
+  int rc = harmonic_matrix(tm, k, j, d.cs, d.sn, d.R, d.ldh, d.B, d.ldb, Stop, Sbot, M, LD);
   if (rc) {
     if (lane == 0) st->rstatus = 2;
     return;
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(32) k_poly_roots(CycleState* st, Dense d, int 
     if (lane == 0) { st->rstatus = 1; st->d = 0; }
     return;
   }
-  int rc = harmonic_matrix(tm, 0, j, d.cs, d.sn, d.R, d.ldh, d.B, nullptr, nullptr, M, LD);
+  int rc = harmonic_matrix(tm, 0, j, d.cs, d.sn, d.R, d.ldh, d.B, d.ldb, nullptr, nullptr, M, LD);
   if (rc) {
     if (lane == 0) { st->rstatus = 2; st->d = 0; }
     return;
@@ -387,6 +387,44 @@ __global__ void __launch_bounds__(32) k_poly_roots(CycleState* st, Dense d, int 
 int launch_cycle_init(CycleState* st, int k, int steps, const double* rnorm2, double target, double2* g,
                       cudaStream_t s) {
   k_cycle_init<<<1, 32, 0, s>>>(st, k, steps, rnorm2, target, g);
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
+// Sec. 3.5: t = ||v^a_{i-1}||^2 - sum_j |b_j|^2 - sum_j |h_j|^2 with the coefficients of the fused
+// reduction; t < -round (round = 8 (i + k + 1) u ||v^a||^2) is a breakdown: the cycle stops with the
+// steps before this one; |t| <= round counts as an invariant subspace (h_{i,i-1} = 0).
+__global__ void __launch_bounds__(32) k_p1_prep(CycleState* st, const double2* h, const double* nva, double tol_u) {
+  const int lane = threadIdx.x & 31;
+  const int stop = st->stop, j = st->j, k = st->k;
+  if (stop) {
+    if (lane == 0) st->p1_skip = 1;
+    return;
+  }
+  double s2 = 0.0;
+  for (int i = lane; i < k + j + 1; i += 32) s2 += abs2(h[i]);
+  for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  if (lane != 0) return;
+  const double n2 = *nva;
+  const double t = n2 - s2;
+  const double round = 8.0 * (double)(j + k + 2) * tol_u * n2;
+  if (!isfinite(t)) {
+    st->stop = 1;
+    st->status |= ST_NONFINITE;
+    st->p1_skip = 1;
+  } else if (t < -round) {
+    st->stop = 1;
+    st->status |= ST_BREAKDOWN;
+    st->p1_skip = 1;
+  } else {
+    st->wnorm2 = t > round ? t : 0.0;
+    st->p1_skip = 0;
+  }
+}
+
+int launch_p1_prep(CycleState* st, const double2* h, const double* nva, double tol_u, cudaStream_t s) {
+  k_p1_prep<<<1, 32, 0, s>>>(st, h, nva, tol_u);
   note_launch();
   COARSE_CUDA(cudaGetLastError());
   return COARSE_OK;

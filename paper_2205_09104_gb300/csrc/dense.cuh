@@ -276,12 +276,12 @@ DENSE_HD inline void leja_order(cd* theta, int d, int* used, cd* out) {
 // M = R_G^{-1} (Q_G^H S)[0:k+j, :], whose eigenvalues nu are 1/theta for the
 // harmonic Ritz values theta (G^H G z = theta G^H S z).
 //   Rh: ld_r, element (row i, col c) = Rh[c*ld_r + i]  (column-major, as built per Arnoldi step)
-//   B : element (i, c) = B[c*k + i]
+//   B : element (i, c) = B[c*ld_b + i]  (column-major with the solver's leading dimension)
 //   Stop: k x k row-major;  Sbot: (j+1) x k row-major
 // Output M (row-major, ld) of size (k+j) x (k+j).
 template <class TM>
 DENSE_HD int harmonic_matrix(const TM& tm, int k, int j, const double* cs, const cd* sn, const cd* Rh, int ld_r,
-                             const cd* B, const cd* Stop, const cd* Sbot, cd* M, int ld) {
+                             const cd* B, int ld_b, const cd* Stop, const cd* Sbot, cd* M, int ld) {
   const int n = k + j;
   const int lane = tm.lane();
   // X = Q^H S, rows 0..n (one extra row kept during the rotation), stored in M's space + scratch row
@@ -320,7 +320,7 @@ DENSE_HD int harmonic_matrix(const TM& tm, int k, int j, const double* cs, const
     }
     for (int i = 0; i < k; ++i) {
       cd s = M[i * ld + c];
-      for (int l = 0; l < j; ++l) s = sub(s, mul(B[l * k + i], M[(k + l) * ld + c]));
+      for (int l = 0; l < j; ++l) s = sub(s, mul(B[l * ld_b + i], M[(k + l) * ld + c]));
       M[i * ld + c] = s;
     }
   }

@@ -66,15 +66,20 @@ int Solver::run_chunk(int j0, int cnt, int kc, void* const* tab) {
   auto issue = [&]() -> int {
     for (int j = j0; j < j0 + cnt; ++j) {
       cur_tag = j;
-      TRY(opA(V[j], V[j + 1], &st->stop));
-      TRY(arnoldi_step(j, kc, tab));
+      if (p1_active) {
+        TRY(p1_step(j, kc, tab));
+      } else {
+        TRY(opA(V[j], V[j + 1], &st->stop));
+        TRY(arnoldi_step(j, kc, tab));
+      }
     }
     return COARSE_OK;
   };
   if (cycles_done < 1 || time_apply) return issue();
   const unsigned long long key = (unsigned long long)j0 | ((unsigned long long)cnt << 8) |
                                  ((unsigned long long)kc << 16) | ((unsigned long long)par << 24) |
-                                 ((unsigned long long)poly_prec << 26) | ((unsigned long long)d << 28);
+                                 ((unsigned long long)poly_prec << 26) | ((unsigned long long)d << 28) |
+                                 ((unsigned long long)(p1_active ? 1 : 0) << 36);
   auto it = graphs.find(key);
   if (it == graphs.end()) {
     if (!cap_stream) COARSE_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
@@ -136,6 +141,16 @@ void Solver::release() {
     if (chunk_ev[i]) { cudaEventDestroy(chunk_ev[i]); chunk_ev[i] = nullptr; }
   if (vecmem) cudaFree(vecmem);
   if (smallmem) cudaFree(smallmem);
+  if (p1mem) cudaFree(p1mem);
+  p1mem = nullptr;
+  Va.clear();
+  VC[0].clear();
+  VC[1].clear();
+  vatab = atab[0] = atab[1] = nullptr;
+  vc_par = vc_updates = vc_k = vc_poly = -1;
+  if (aux_stream) { cudaStreamDestroy(aux_stream); aux_stream = nullptr; }
+  if (ev_fork) { cudaEventDestroy(ev_fork); ev_fork = nullptr; }
+  if (ev_join) { cudaEventDestroy(ev_join); ev_join = nullptr; }
   if (st_host) cudaFreeHost(st_host);
   vecmem = nullptr;
   smallmem = nullptr;
@@ -215,6 +230,9 @@ int Solver::ensure(int m, int k, int dmax) {
   one_acc = put({acc});
   one_t = put({t});
   COARSE_CUDA(cudaMemcpyAsync(tabs, host.data(), host.size() * sizeof(void*), cudaMemcpyHostToDevice, stream));
+  tabs_base = tabs;
+  tabs_used = host.size();
+  tabs_cap = 16 * (size_t)(2 * maxq + 8) * sizeof(double2) / sizeof(void*);
   COARSE_CUDA(cudaMallocHost((void**)&st_host, sizeof(CycleState) + 4 * sizeof(int)));
   stop_host = (int*)(st_host + 1);
   for (int i = 0; i < 2; ++i)
@@ -317,6 +335,83 @@ int Solver::read_state() {
   return COARSE_OK;
 }
 
+// Storage of the pipelined process: Va (m + 1 vectors), VC (2 x k), their pointer tables.
+int Solver::ensure_p1() {
+  if (p1mem) return COARSE_OK;
+  const size_t vbytes = csize(v64) * (size_t)N;
+  const size_t nvec = (size_t)(m_cap + 1) + 2 * (size_t)k_cap;
+  TRY(dalloc((char**)&p1mem, nvec * vbytes));
+  char* p = (char*)p1mem;
+  auto take = [&]() { void* q = p; p += vbytes; return q; };
+  Va.assign(m_cap + 1, nullptr);
+  for (int i = 0; i <= m_cap; ++i) Va[i] = take();
+  for (int b = 0; b < 2; ++b) {
+    VC[b].assign(k_cap, nullptr);
+    for (int i = 0; i < k_cap; ++i) VC[b][i] = take();
+  }
+  std::vector<void*> host;
+  host.insert(host.end(), Va.begin(), Va.end());
+  for (int b = 0; b < 2; ++b) {
+    host.insert(host.end(), VC[b].begin(), VC[b].end());
+    host.insert(host.end(), Va.begin(), Va.end());
+  }
+  if (tabs_used + host.size() > tabs_cap) {
+    set_error("pipelined Arnoldi: pointer table overflow");
+    return COARSE_ERR_INVALID_ARG;
+  }
+  void** at = tabs_base + tabs_used;
+  vatab = at;
+  atab[0] = at + (m_cap + 1);
+  atab[1] = atab[0] + k_cap + (m_cap + 1);
+  COARSE_CUDA(cudaMemcpyAsync(at, host.data(), host.size() * sizeof(void*), cudaMemcpyHostToDevice, stream));
+  tabs_used += host.size();
+  if (!aux_stream) COARSE_CUDA(cudaStreamCreateWithFlags(&aux_stream, cudaStreamNonBlocking));
+  if (!ev_fork) COARSE_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  if (!ev_join) COARSE_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+  COARSE_CUDA(cudaStreamSynchronize(stream));
+  return COARSE_OK;
+}
+
+// VC[par][i] = A C[par][i] (Sec. 3.5, the recycle vectors' images under the preconditioned
+// operator), recomputed whenever the recycle space or the polynomial changed.
+int Solver::ensure_vc(int kc) {
+  if (vc_par == par && vc_updates == updates && vc_k == kc && vc_poly == poly_builds * 4 + poly_prec) return COARSE_OK;
+  for (int c = 0; c < kc; ++c) TRY(opA(C[par][c], VC[par][c], nullptr));
+  vc_par = par;
+  vc_updates = updates;
+  vc_k = kc;
+  vc_poly = poly_builds * 4 + poly_prec;
+  return COARSE_OK;
+}
+
+// Step j of a latency-1 pipelined cycle (Sec. 3.5, Alg. "pipe1fgmres" / "pipe1gcrodr", sigma = 0):
+// the fused reduction h = [C, V_0..V_j]^H Va[j], ||Va[j]||^2 runs on aux_stream while the product
+// w = A Va[j] -> Va[j+1] runs on `stream`; then t = ||Va[j]||^2 - sum |h|^2 (breakdown if negative),
+// V[j+1] = Va[j] - [C, V] h and Va[j+1] = w - [VC, Va] h with the same coefficients, the column's
+// Givens update, and both divided by h_{j+1,j} = sqrt(t).
+int Solver::p1_step(int j, int kc, void* const* tab) {
+  const int* stop = &st->stop;
+  const int nq = kc + j + 1;
+  double* nva = norm2 + 4;
+  void* const* at = kc > 0 ? atab[par] : vatab;
+  COARSE_CUDA(cudaEventRecord(ev_fork, stream));
+  COARSE_CUDA(cudaStreamWaitEvent(aux_stream, ev_fork, 0));
+  TRY(launch_multidot(v64, (const void* const*)tab, nq, Va[j], N, h1, nva, partial, counter, stop, aux_stream));
+  COARSE_CUDA(cudaEventRecord(ev_join, aux_stream));
+  TRY(opA(Va[j], Va[j + 1], stop));
+  COARSE_CUDA(cudaStreamWaitEvent(stream, ev_join, 0));
+  TRY(launch_p1_prep(st, h1, nva, v64 ? 0x1p-53 : 0x1p-24, stream));
+  // the recurrences run whenever t was usable (also on the step whose finalize then stops the cycle)
+  TRY(launch_scale(v64, Va[j], nullptr, make_double2(1.0, 0.0), V[j + 1], N, &st->p1_skip, 0, stream));
+  TRY(launch_update(v64, (const void* const*)tab, nq, h1, 1, V[j + 1], N, 0, nullptr, nullptr, partial, counter,
+                    &st->p1_skip, stream));
+  TRY(launch_update(v64, (const void* const*)at, nq, h1, 1, Va[j + 1], N, 0, nullptr, nullptr, partial, counter,
+                    &st->p1_skip, stream));
+  TRY(launch_step_finalize(st, h1, nullptr, dn, stream));
+  TRY(launch_scale(v64, V[j + 1], &st->inv_h, make_double2(1.0, 0.0), V[j + 1], N, &st->j, j + 1, stream));
+  return launch_scale(v64, Va[j + 1], &st->inv_h, make_double2(1.0, 0.0), Va[j + 1], N, &st->j, j + 1, stream);
+}
+
 // Orthogonalise V[j+1] against [C (kc), V_0..V_j] twice (CGS2, one fused reduction per pass),
 // then finalize the Arnoldi column and normalise.
 int Solver::arnoldi_step(int j, int kc, void* const* tab) {
@@ -335,6 +430,7 @@ int Solver::arnoldi_step(int j, int kc, void* const* tab) {
 
 int Solver::build_poly(const double2* start64, uint64_t seed, int dd) {
   clear_graphs();  // graphs bake host-side chain constants (theta_1 for degree 1)
+  ++poly_builds;
   poly_ok = false;
   d = 0;
   if (dd <= 0) { poly_ok = true; return COARSE_OK; }
@@ -395,8 +491,16 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
     void* const* tab = kc > 0 ? qtab[par] : vtab;
     // a cycle that is to yield the first recycle space runs all m steps (no least-squares stop)
     const bool extract_full = full_first && kc == 0 && kdef > 0 && updates < ulimit;
+    // pipelined cycles (Sec. 3.5): every cycle of pipelined GMRES; the cycles of GCRO-DR that have
+    // a recycle space (its first cycle is the classical GMRES cycle)
+    p1_active = pipelined && (kdef == 0 || kc > 0);
+    if (p1_active) {
+      TRY(ensure_p1());
+      if (kc > 0) TRY(ensure_vc(kc));
+    }
     TRY(launch_cycle_init(st, kc, steps, norm2, extract_full ? 0.0 : target_abs, dn.g, stream));
     TRY(launch_scale(v64, r, &st->inv_h, make_double2(1.0, 0.0), V[0], N, &st->stop, 0, stream));
+    if (p1_active) TRY(opA(V[0], Va[0], &st->stop));  // v^a_0 = A v_0
     // Steps go out in chunks; the stop flag of chunk c-1 is read back (async copy +
     // event) while chunk c runs, so at most one chunk of gated launches follows a stop.
     constexpr int kChunk = 4;
@@ -427,6 +531,7 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
       return COARSE_ERR_NONFINITE;
     }
     if (cs.status & ST_ZERO) return COARSE_OK;  // zero residual
+    if (cs.status & ST_BREAKDOWN) info->breakdowns++;
     const int j = cs.j;
     info->iterations += j;
     info->last_resid = cs.resid;
@@ -610,6 +715,7 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
   const long long launches0 = launches_so_far();
   s->time_apply = (p->flags & COARSE_TIME_APPLY) != 0;
   s->full_first = (p->flags & COARSE_RECYCLE_FULL_CYCLE) != 0;
+  s->pipelined = (p->flags & COARSE_PIPELINED) != 0;
   s->apply_ms = 0.0;
   s->apply_bytes = 0.0;
   s->apply_count = 0;
@@ -673,6 +779,7 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
     inf.ir_steps++;
     inf.cycles += ii.cycles;
     inf.iterations += ii.iterations;
+    inf.breakdowns += ii.breakdowns;
     TRY(residual());
     COARSE_CUDA(cudaMemcpyAsync(hn, op->norms, sizeof(double), cudaMemcpyDeviceToHost, stream));
     COARSE_CUDA(cudaStreamSynchronize(stream));

@@ -14,6 +14,7 @@ struct InnerInfo {
   int cycles = 0;
   int iterations = 0;
   int recycle_failures = 0;
+  int breakdowns = 0;  // pipelined cycles ended by t < 0 (Sec. 3.5)
   double last_resid = 0.0;
 };
 
@@ -75,6 +76,25 @@ struct Solver {
   // `prec`); the recycle space belongs to the preconditioned operator of `rec_poly_prec`
   // COARSE_RECYCLE_FULL_CYCLE: while no recycle space is held, cycles run all their steps
   bool full_first = false;
+  // COARSE_PIPELINED (Sec. 3.5): latency-1 pipelined Arnoldi.  Va[i] = A V[i] alongside the basis,
+  // VC[p][j] = A C[p][j] for the recycle vectors; the reduction of a step runs on aux_stream while
+  // the stencil of the same step runs on `stream`.
+  bool pipelined = false;
+  bool p1_active = false;                // the current cycle is a pipelined one
+  void* p1mem = nullptr;
+  std::vector<void*> Va;
+  std::vector<void*> VC[2];
+  void** vatab = nullptr;                // [Va_0..Va_m]
+  void** atab[2] = {nullptr, nullptr};   // [VC[p], Va_0..Va_m]
+  int vc_par = -1, vc_updates = -1, vc_k = -1, vc_poly = -1;   // what VC was computed for
+  int poly_builds = 0;
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  void** tabs_base = nullptr;
+  size_t tabs_used = 0, tabs_cap = 0;
+  int ensure_p1();
+  int ensure_vc(int kc);
+  int p1_step(int j, int kc, void* const* tab);
   int poly_prec = COARSE_PREC_FP32;
   int rec_poly_prec = -1;
   // odd-even: the Krylov operator is S = 1 - D_ee^{-1} D_eo D_oo^{-1} D_oe on the even sites
@@ -111,6 +131,7 @@ struct Solver {
   int recycle_check(double out[4]);
   void invalidate() {
     clear_graphs();
+    vc_par = vc_updates = vc_k = vc_poly = -1;
     poly_ok = false;
     d = 0;
     k_cur = 0;

@@ -12,7 +12,7 @@ constexpr int kMaxPoly = 32;                  // largest polynomial degree d
 constexpr int kPolyScale = 3 * kMaxDense;     // slot of 1/theta_1 in the chain table
 
 // status bits of a cycle
-enum : int { ST_LUCKY = 1, ST_NONFINITE = 2, ST_ZERO = 4 };
+enum : int { ST_LUCKY = 1, ST_NONFINITE = 2, ST_ZERO = 4, ST_BREAKDOWN = 8 };
 
 struct CycleState {
   int j;        // Arnoldi steps done in this cycle
@@ -22,7 +22,7 @@ struct CycleState {
   int status;   // ST_* bits
   int rstatus;  // result of k_recycle / k_poly_roots (0 = ok)
   int d;        // polynomial degree found by k_poly_roots
-  int pad;
+  int p1_skip;  // pipelined step: 1 when this step's vector recurrences must not run
   double beta;    // ||r|| at the start of the cycle
   double target;  // least-squares residual that ends the cycle
   double resid;   // current least-squares residual |g_{j+1}|
@@ -53,6 +53,10 @@ struct Dense {
 int launch_cycle_init(CycleState* st, int k, int steps, const double* rnorm2, double target, double2* g,
                       cudaStream_t s);
 int launch_step_finalize(CycleState* st, const double2* h1, const double2* h2, const Dense& d, cudaStream_t s);
+// Latency-1 pipelined Arnoldi (Sec. 3.5): from the fused reduction of step i (h = [C, V]^H v^a_{i-1}
+// and ||v^a_{i-1}||^2) form t = ||v^a||^2 - sum |h|^2 into st->wnorm2 for the finalize; t below
+// minus its rounding (tol_u: unit roundoff of the vectors) is a breakdown that stops the cycle.
+int launch_p1_prep(CycleState* st, const double2* h, const double* nva, double tol_u, cudaStream_t s);
 int launch_cycle_solve(const CycleState* st, const Dense& d, cudaStream_t s);
 int launch_recycle(CycleState* st, const Dense& d, const double2* SW, int ldsw, int knew, cudaStream_t s);
 int launch_poly_roots(CycleState* st, const Dense& d, int dmax, cudaStream_t s);

@@ -164,6 +164,18 @@ class CoarseOp:
             return None
         return u[: k.value], c[: k.value]
 
+    def recycle_set(self, precision: int, u: torch.Tensor | None, c: torch.Tensor | None, updates: int,
+                    odd_even: bool = False, adjoint: bool = False, stream=None):
+        """Install a recycle space ([k, N] tensors of the inner precision; None drops it)."""
+        k = 0 if u is None else int(u.shape[0])
+        if k:
+            dt = _PREC_DT[precision]
+            for t in (u, c):
+                if not (t.is_cuda and t.dtype == dt and t.is_contiguous() and t.shape == u.shape):
+                    raise ValueError(f"u and c must be contiguous CUDA tensors of dtype {dt} and one shape")
+        check(lib().coarse_recycle_set(self.handle, precision, int(odd_even), int(adjoint),
+                                       _ptr(u) if k else None, _ptr(c) if k else None, k, updates, _stream(stream)))
+
     def poly(self, precision: int):
         buf = (ctypes.c_double * 64)()
         d = ctypes.c_int()

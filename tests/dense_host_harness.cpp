@@ -68,4 +68,54 @@ void host_givens(const double* x, const double* y, double* out /* c, s.re, s.im,
   out[0] = c; out[1] = s.x; out[2] = s.y; out[3] = r.x; out[4] = r.y;
 }
 
+// The harmonic Ritz matrix of an augmented GCRO-DR cycle (dense.cuh harmonic_matrix): G = [[I_k, B],
+// [0, Hbar]] with Hbar (j+1) x j and B k x j (both row-major, interleaved), S = [[Stop, 0],
+// [Sbot, I]]; Hbar is reduced by Givens rotations exactly as the solver's per-step finalize does,
+// B is handed over with leading dimension ld_b >= k (as the solver stores it).  Returns the k+j
+// eigenvalues nu of M = R_G^{-1} (Q_G^H S) in nu (2*(k+j) doubles).
+int host_harmonic_nu(int k, int j, int ld_b, const double* hbar, const double* b, const double* stop,
+                     const double* sbot, double* nu) {
+  const int n = k + j, ldh = j + 1, ld = n + 1;
+  std::vector<cd> R(ldh * j), Bc(ld_b * (j > 0 ? j : 1), mk(0.0, 0.0)), col(j + 2), sn(j), M(ld * ld);
+  std::vector<double> cs(j);
+  const cd* H = reinterpret_cast<const cd*>(hbar);
+  for (int c = 0; c < j; ++c) {
+    for (int i = 0; i <= c + 1; ++i) col[i] = H[i * j + c];
+    for (int i = 0; i < c; ++i) {
+      const cd u = col[i], w = col[i + 1];
+      col[i] = add(scal(u, cs[i]), mul(sn[i], w));
+      col[i + 1] = sub(scal(w, cs[i]), conjmul(sn[i], u));
+    }
+    double cc;
+    cd sg, r;
+    givens(col[c], col[c + 1], cc, sg, r);
+    cs[c] = cc;
+    sn[c] = sg;
+    col[c] = r;
+    for (int i = 0; i <= c; ++i) R[c * ldh + i] = col[i];
+  }
+  const cd* Bi = reinterpret_cast<const cd*>(b);
+  for (int c = 0; c < j; ++c)
+    for (int i = 0; i < k; ++i) Bc[c * ld_b + i] = Bi[i * j + c];
+  HostTeam tm;
+  int rc = harmonic_matrix(tm, k, j, cs.data(), sn.data(), R.data(), ldh, Bc.data(), ld_b,
+                           reinterpret_cast<const cd*>(stop), reinterpret_cast<const cd*>(sbot), M.data(), ld);
+  if (rc) return rc;
+  std::vector<cd> A(n * n), Z(n * n), v(n);
+  std::vector<double> sc(8);
+  for (int i = 0; i < n; ++i)
+    for (int c = 0; c < n; ++c) {
+      A[i * n + c] = M[i * ld + c];
+      Z[i * n + c] = mk(i == c ? 1.0 : 0.0, 0.0);
+    }
+  hessenberg(tm, A.data(), Z.data(), n, n, v.data(), sc.data());
+  rc = schur_qr(tm, A.data(), Z.data(), n, n, false);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    nu[2 * i] = A[i * n + i].x;
+    nu[2 * i + 1] = A[i * n + i].y;
+  }
+  return 0;
+}
+
 }  // extern "C"

@@ -31,6 +31,7 @@ def lib(tmp_path_factory):
     L.host_hessenberg.argtypes = [ctypes.c_int, dp, dp, dp]
     L.host_leja.argtypes = [ctypes.c_int, dp]
     L.host_givens.argtypes = [dp, dp, dp]
+    L.host_harmonic_nu.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp]
     return L
 
 
@@ -118,3 +119,35 @@ def test_leja_matches_oracle_and_golden(lib):
     th = np.array([1, -2, 3j, 0.5, 2 + 2j], dtype=complex)
     lib.host_leja(5, _p(th.view(np.float64)))
     assert np.array_equal(th, np.array([3j, -2, 2 + 2j, 1, 0.5]))
+
+
+@pytest.mark.parametrize("k,j,ld_b", [(4, 8, 32), (3, 10, 32), (32, 18, 32), (1, 5, 7)])
+def test_harmonic_matrix_of_augmented_cycle(lib, k, j, ld_b):
+    """Eigenvalues of the solver's harmonic Ritz matrix of a GCRO-DR cycle (Sec. 3.4) are 1/theta
+    for the generalized problem G^H G z = theta G^H S z (SciPy QZ), with B stored at the solver's
+    leading dimension (ld_b != k checks that the matrix is read with it)."""
+    import scipy.linalg as sla
+    rng = np.random.default_rng(100 * k + j)
+    cplx = lambda *sh: rng.standard_normal(sh) + 1j * rng.standard_normal(sh)
+    Hb = np.triu(cplx(j + 1, j), -1)
+    Hb[np.arange(1, j + 1), np.arange(j)] = np.abs(Hb[np.arange(1, j + 1), np.arange(j)]) + 0.5
+    B = cplx(k, j)
+    Stop = np.eye(k) + 0.3 * cplx(k, k)
+    Sbot = 0.3 * cplx(j + 1, k)
+    G = np.zeros((k + j + 1, k + j), complex)
+    G[:k, :k] = np.eye(k)
+    G[:k, k:] = B
+    G[k:, k:] = Hb
+    S = np.zeros((k + j + 1, k + j), complex)
+    S[:k, :k] = Stop
+    S[k:, :k] = Sbot
+    S[k:, k:] = np.eye(j + 1, j)
+    nu = np.zeros(2 * (k + j))
+    rc = lib.host_harmonic_nu(k, j, ld_b, _p(np.ascontiguousarray(Hb)), _p(np.ascontiguousarray(B)),
+                              _p(np.ascontiguousarray(Stop)), _p(np.ascontiguousarray(Sbot)), _p(nu))
+    assert rc == 0
+    theta = 1.0 / (nu[0::2] + 1j * nu[1::2])
+    ref = sla.eig(G.conj().T @ G, G.conj().T @ S, right=False)
+    ref = ref[np.isfinite(ref)]
+    for t in ref:
+        assert np.abs(theta - t).min() <= 1e-9 * max(1.0, abs(t)), (t, theta)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import (abs_apply, abs_apply_at, assert_entrywise, bf16_blocks_of, bf16_operator, make_op, rel,
+from gpu_helpers import (abs_apply, abs_apply_at, assert_entrywise, bf16, bf16_blocks_of, bf16_operator, make_op, rel,
                          rhs, site_blocks, stencil_factor, to_cuda)
 from oracle import coarse as ocoarse
 
@@ -41,16 +41,20 @@ def test_apply_matches_oracle(ops, nv, prec, mu):
     dt = torch.complex128 if prec == 0 else torch.complex64
     y = dev.apply(torch.from_numpy(X).to("cuda", dt), precision=prec).cpu().numpy()
     s, h = op.self_blocks.numpy(), op.hop_blocks.numpy()
+    s3v = np.tile(ocoarse.sigma3(op.n // 2), op.volume)
     for c in range(3):
         ref = ocoarse.apply(s, h, op.dims, X[c], mu)
         assert rel(y[c], ref) <= TOL[prec], (nv, prec, mu, c)
-        bound = stencil_factor(prec, op.n) * abs_apply(s, h, op.dims, X[c], mu)
+        # three BF16 columns run the tensor-core multi-right-hand-side kernel, which also rounds x to BF16
+        xp = "bf16" if prec == 2 else None
+        bound = stencil_factor(prec, op.n, x_prec=xp) * abs_apply(s, h, op.dims, X[c], mu)
         assert_entrywise(y[c], ref, bound, f"nv={nv} prec={prec} mu={mu} column {c}")
         if prec == 2:
             sr, hr = bf16_operator(s, h, op.dims)
             x32 = X[c].astype(np.complex64).astype(np.complex128)
-            ref_r = ocoarse.apply(sr, hr, op.dims, x32, mu)
-            bound = stencil_factor(2, op.n, rounded_operands=True) * abs_apply(sr, hr, op.dims, x32, mu)
+            ref_r = ocoarse.apply(sr, hr, op.dims, bf16(x32), 0.0) + 1j * mu * s3v * x32
+            bound = stencil_factor(2, op.n, rounded_operands=True) * (abs_apply(sr, hr, op.dims, bf16(x32))
+                                                                      + mu * np.abs(x32))
             assert_entrywise(y[c], ref_r, bound, f"nv={nv} bf16 rounded operands mu={mu} column {c}")
 
 

@@ -2,8 +2,12 @@
 
 The recycle space is read back with coarse_recycle_get and checked three ways:
   * FP64: range(U_k) and range(C_k) equal the oracle's after one and after two cycles
-    (largest principal-angle sine <= 1e-8; the spaces are unique for a fixed Krylov space
-    when the k-th and (k+1)-th harmonic Ritz moduli are apart, 0.61 vs 0.87 here);
+    (largest principal-angle sine <= 1e-6; the spaces are unique for a fixed Krylov space
+    when the k-th and (k+1)-th harmonic Ritz moduli are apart: 0.61 vs 0.87 after the first
+    cycle, 0.235 vs 0.31 after the second.  The bound is set by the polynomial: its roots,
+    harmonic Ritz values of a non-normal 4 x 4 problem, agree with the oracle's to about 1e-8,
+    which moves the preconditioned operator, and so the spaces, at that level; a different
+    choice of k vectors moves them by O(0.1));
   * the relations A U_k = C_k and C_k^H C_k = I, recomputed by the oracle from the
     vectors the GPU holds (A = D q(D) with the GPU's own Leja roots), and reported by the
     device-side check coarse_recycle_check;
@@ -63,8 +67,8 @@ def test_recycle_space_matches_oracle_fp64(wilson4, cycles):
     M = lambda v: krylov.poly_apply(D, theta, v)
     _, info, rec = krylov.gcrodr(D, b, m=m, k=k, tol=1e-10, max_cycles=cycles, precond=M, u_limit=10)
     assert rec.updates == cycles
-    assert _sin_max_angle(Ug, rec.U) <= 1e-8
-    assert _sin_max_angle(Cg, rec.C) <= 1e-8
+    assert _sin_max_angle(Ug, rec.U) <= 1e-6
+    assert _sin_max_angle(Cg, rec.C) <= 1e-6
     # the relations, recomputed by the oracle with the GPU's roots
     Mg = lambda v: krylov.poly_apply(D, dev.poly(PREC_FP64), v)
     AU = np.array([D(Mg(u)) for u in Ug.T]).T
