@@ -678,11 +678,12 @@ __global__ void __launch_bounds__(kEoRingThreads, 1) k_eo_ring(EoArgs a, int S) 
         if (!ok) break;
       }
     }
-    if (!ok && lane == 0) {
-      // the consumers stopped: drain the copies still in flight (the last S issued)
-      atomicExch(a.err, 1);
+    if (!ok && lane == 0) atomicExch(a.err, 1);
+    // The copies of the last stages issued must have landed before the CTA exits, also when every
+    // copy was issued and the consumers then stopped on a timeout of their own: wait (bounded) on
+    // their full barriers.  After a normal run these phases are complete and the waits return at once.
+    if (lane == 0)
       for (int j = max(0, issued - S); j < issued; ++j) mbar_wait(full + j % S, (uint32_t)((j / S) & 1));
-    }
     return;
   }
 
