@@ -276,8 +276,10 @@ int coarse_solve_adjoint(coarse_op* op, const void* b, void* x, int nrhs, const 
 /*
  * coarse_solve_batched -- nops independent solves (operators of uneven size),
  * advanced together: every Krylov phase of all unfinished solves runs in one
- * kernel launch, the launch sequence of one step is captured once in a CUDA
- * graph and replayed.  ops[i], b[i], x[i], nrhs[i] as in coarse_solve; all
+ * kernel launch, and the whole lockstep solve (all refinement steps, cycles and
+ * Arnoldi steps) is one CUDA graph, launched once, whose nested conditional WHILE
+ * nodes are driven by control kernels on the device (bounded by max_ir,
+ * max_restarts and m).  ops[i], b[i], x[i], nrhs[i] as in coarse_solve; all
  * operators use the same params.  infos: host array of sum(nrhs) records in
  * (operator, column) order.  Synchronises `stream`.
  * Each solve follows Sec. 3.6 exactly as coarse_solve does (restarted GMRES,

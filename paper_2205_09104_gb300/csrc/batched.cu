@@ -3,11 +3,11 @@
 // Every (operator, right-hand-side column) is one solve.  Setup (polynomial and the first
 // u recycle-space updates) runs per operator through the single-operator solver; the solves
 // then share their operator's blocks, polynomial and frozen U_k, C_k.  In the lockstep phase
-// each Krylov phase is ONE kernel launch over all solves (per n-group for the stencil), the
-// launch sequence of one Arnoldi step is captured once in a CUDA graph and replayed for
-// every step (the kernels read the step index from a device counter), and per-solve stop /
-// active / done flags on the device skip the solves that are finished.  The host reads one
-// array of cycle states per cycle and one array of norms per refinement step.
+// each Krylov phase is ONE kernel launch over all solves (per n-group for the stencil), and
+// per-solve stop / active / done flags on the device skip the solves that are finished.  The
+// whole lockstep solve -- every refinement step, cycle and Arnoldi step -- is one CUDA graph
+// launched once: three nested conditional WHILE nodes whose conditions control kernels set on
+// the device (with iteration bounds), so the host waits only for the end of the batch.
 #include <math.h>
 #include <string.h>
 
@@ -70,25 +70,18 @@ struct Batch {
   BSolve* dS = nullptr;
   int* step = nullptr;
   CycleState* states = nullptr;
-  CycleState* states_h = nullptr;
   double* norms = nullptr;
-  double* norms_h = nullptr;
   int* flags = nullptr;
-  int* flags_h = nullptr;
   int* chunk_off = nullptr;
   std::vector<Group> groups;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
   long long launches = 0;
 
   ~Batch() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
     if (mem) cudaFree(mem);
-    if (states_h) cudaFreeHost(states_h);
   }
 
   // one stencil phase over all n-groups (chain: a polynomial-chain phase, on the chain's blocks)
@@ -179,6 +172,179 @@ struct Batch {
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// ---- device-side control of the whole batched solve (refinement steps, cycles, Arnoldi steps)
+//
+// The whole lockstep solve is one CUDA graph: three nested conditional WHILE nodes (refinement
+// step > cycle > Arnoldi step) whose conditions are set by the control kernels below from the
+// per-solve state on the device, each with its own iteration bound, so that the host launches
+// the graph once and reads the per-solve results at the end.
+
+struct BCtl {
+  int ir, cyc, steps_run, cycles_run;  // loop counters (steps_run, cycles_run: totals, for accounting)
+  int max_ir, max_cyc, steps_max;
+  double tol, inner_tol;
+  cudaGraphConditionalHandle h_ir, h_cyc, h_step;
+};
+
+struct BInfo {
+  int status, iterations, cycles, ir_steps;
+  double bn, rn;
+};
+
+constexpr int kCtlThreads = 1024;
+
+__device__ int ctl_any(int v) {
+  return __syncthreads_or(v);
+}
+
+// after the initial residual: ||b||, ||r||, solves already done, and the refinement loop's condition
+__global__ void __launch_bounds__(kCtlThreads) kb_ctl_start(BCtl* c, const BSolve* S, BInfo* I, int ns) {
+  int left = 0;
+  for (int q = threadIdx.x; q < ns; q += blockDim.x) {
+    const double* n2 = S[q].norm2;
+    int* fl = S[q].flags;
+    const double bn = sqrt(fmax(n2[2], 0.0)), rn = sqrt(fmax(n2[1], 0.0));
+    BInfo in{};
+    in.bn = bn;
+    in.rn = rn;
+    int done;
+    if (!isfinite(bn) || !isfinite(rn)) {
+      in.status = COARSE_ERR_NONFINITE;
+      done = 1;
+    } else {
+      done = (bn == 0.0 || rn <= c->tol * bn) ? 1 : 0;
+    }
+    I[q] = in;
+    fl[0] = 0;
+    fl[1] = done;
+    left |= !done;
+  }
+  left = ctl_any(left);
+  if (threadIdx.x == 0) {
+    c->ir = c->cyc = c->steps_run = c->cycles_run = 0;
+    cudaGraphSetConditional(c->h_ir, (left && c->max_ir > 0) ? 1u : 0u);
+  }
+}
+
+// start of a refinement step: the unfinished solves become inner-active with their inner targets
+__global__ void __launch_bounds__(kCtlThreads) kb_ir_begin(BCtl* c, const BSolve* S, const BInfo* I, int ns) {
+  int act = 0;
+  for (int q = threadIdx.x; q < ns; q += blockDim.x) {
+    int* fl = S[q].flags;
+    const int a = !fl[1];
+    fl[0] = a;
+    S[q].norm2[3] = fmax(c->inner_tol, 0.5 * c->tol * I[q].bn / fmax(I[q].rn, 1e-300));
+    act |= a;
+  }
+  act = ctl_any(act);
+  if (threadIdx.x == 0) {
+    c->cyc = 0;
+    cudaGraphSetConditional(c->h_cyc, (act && c->max_cyc > 0) ? 1u : 0u);
+  }
+}
+
+// after a cycle's start: Arnoldi steps run while some cycle runs and fewer than steps_max were taken
+__global__ void __launch_bounds__(kCtlThreads) kb_step_gate(BCtl* c, const BSolve* S, const int* step, int ns,
+                                                            int count_step) {
+  int run = 0;
+  for (int q = threadIdx.x; q < ns; q += blockDim.x) run |= S[q].st->stop == 0;
+  run = ctl_any(run);
+  if (threadIdx.x == 0) {
+    if (count_step) c->steps_run++;
+    cudaGraphSetConditional(c->h_step, (run && *step < c->steps_max) ? 1u : 0u);
+  }
+}
+
+// end of a cycle: statistics, solves that leave the inner loop, the cycle loop's condition
+__global__ void __launch_bounds__(kCtlThreads) kb_cycle_end(BCtl* c, const BSolve* S, BInfo* I, int ns) {
+  int act = 0;
+  for (int q = threadIdx.x; q < ns; q += blockDim.x) {
+    int* fl = S[q].flags;
+    if (!fl[0]) continue;
+    const CycleState& cs = *S[q].st;
+    I[q].cycles++;
+    I[q].iterations += cs.j;
+    if (cs.status & ST_NONFINITE) {
+      I[q].status = COARSE_ERR_NONFINITE;
+      fl[1] = 1;
+      fl[0] = 0;
+      continue;
+    }
+    if (cs.j == 0 || cs.resid <= cs.target || (cs.status & (ST_LUCKY | ST_ZERO))) fl[0] = 0;
+    act |= fl[0];
+  }
+  act = ctl_any(act);
+  if (threadIdx.x == 0) {
+    c->cyc++;
+    c->cycles_run++;
+    cudaGraphSetConditional(c->h_cyc, (act && c->cyc < c->max_cyc) ? 1u : 0u);
+  }
+}
+
+// end of a refinement step: new true residuals, solves that met the tolerance, the loop's condition
+__global__ void __launch_bounds__(kCtlThreads) kb_ir_end(BCtl* c, const BSolve* S, BInfo* I, int ns) {
+  int left = 0;
+  for (int q = threadIdx.x; q < ns; q += blockDim.x) {
+    int* fl = S[q].flags;
+    if (fl[1]) continue;
+    I[q].ir_steps++;
+    const double rn = sqrt(fmax(S[q].norm2[1], 0.0));
+    I[q].rn = rn;
+    if (!isfinite(rn)) {
+      I[q].status = COARSE_ERR_NONFINITE;
+      fl[1] = 1;
+    } else if (rn <= c->tol * I[q].bn) {
+      fl[1] = 1;
+    }
+    left |= !fl[1];
+  }
+  left = ctl_any(left);
+  if (threadIdx.x == 0) {
+    c->ir++;
+    cudaGraphSetConditional(c->h_ir, (left && c->ir < c->max_ir) ? 1u : 0u);
+  }
+}
+
+// Adds a WHILE node on `handle` at the capture position of `s` and returns its (empty) body.
+int add_while(cudaStream_t s, cudaGraphConditionalHandle handle, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  COARSE_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &nd));
+  if (cst != cudaStreamCaptureStatusActive) {
+    set_error("coarse_solve_batched: stream is not capturing");
+    return COARSE_ERR_CUDA;
+  }
+  cudaGraphNodeParams prm{};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = handle;
+  prm.conditional.type = cudaGraphCondTypeWhile;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  COARSE_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
+  *body = prm.conditional.phGraph_out[0];
+  COARSE_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return COARSE_OK;
+}
+
+// Captures fill(stream) into the body graph of a conditional node.
+template <class F>
+int capture_body(cudaGraph_t body, cudaStream_t cs, F&& fill) {
+  COARSE_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int rc = fill(cs);
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &out);
+  if (rc == COARSE_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture (conditional body)");
+  return rc;
+}
+
+size_t graph_kernels(cudaGraph_t g) {
+  size_t n = 0;
+  cudaGraphGetNodes(g, nullptr, &n);
+  return n;
+}
 
 }  // namespace
 }  // namespace coarse
@@ -299,6 +465,8 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   const size_t o_S = take(sizeof(BSolve) * ns);
   const size_t o_coff = take(sizeof(int) * (ns + 1));
   const size_t o_groups = take(sizeof(int) * (2 * ns + 8) * 3);
+  const size_t o_ctl = take(sizeof(BCtl));
+  const size_t o_info = take(sizeof(BInfo) * ns);
   // multi-RHS stencil phases: BF16 inner solves, every operator carrying the fragment-layout
   // blocks (created with max_nrhs > 1) and at most 12 columns
   B.mrhs = prec == COARSE_PREC_BF16;
@@ -345,9 +513,6 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
     return COARSE_ERR_OOM;
   }
   COARSE_CUDA(cudaMemsetAsync(B.mem, 0, bytes, s));
-  COARSE_CUDA(cudaMallocHost((void**)&B.states_h, sizeof(CycleState) * ns + sizeof(double) * 4 * ns + sizeof(int) * 2 * ns + 64));
-  B.norms_h = reinterpret_cast<double*>(B.states_h + ns);
-  B.flags_h = reinterpret_cast<int*>(B.norms_h + 4 * ns);
   B.step = reinterpret_cast<int*>(B.mem + o_step);
   B.states = reinterpret_cast<CycleState*>(B.mem + o_states);
   B.norms = reinterpret_cast<double*>(B.mem + o_norms);
@@ -558,146 +723,124 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   int kmin = m;
   for (int q = 0; q < ns; ++q) kmin = std::min(kmin, hs[q].kc);
   B.steps_max = kmin > 0 ? m - kmin : m;
-  COARSE_CUDA(cudaEventCreateWithFlags(&B.ev[0], cudaEventDisableTiming));
-  COARSE_CUDA(cudaEventCreateWithFlags(&B.ev[1], cudaEventDisableTiming));
   COARSE_CUDA(cudaStreamSynchronize(s));
 
-  // ---- the Arnoldi step as a CUDA graph
-  {
-    cudaStream_t cs;
-    COARSE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    int rc = e == cudaSuccess ? B.step_sequence(cs) : cuda_fail(e, "cudaStreamBeginCapture");
-    cudaError_t e2 = cudaStreamEndCapture(cs, &B.graph);
-    if (rc == COARSE_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
-    if (rc == COARSE_OK) {
-      e2 = cudaGraphInstantiate(&B.gexec, B.graph, 0);
-      if (e2 != cudaSuccess) rc = cuda_fail(e2, "cudaGraphInstantiate");
+  // ---- the whole lockstep solve as one CUDA graph with device-side control
+  BCtl* dctl = reinterpret_cast<BCtl*>(B.mem + o_ctl);
+  BInfo* dinfo = reinterpret_cast<BInfo*>(B.mem + o_info);
+  cudaStream_t cs[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (auto& q : cs) COARSE_CUDA(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+  struct StreamsGuard {
+    cudaStream_t* q;
+    ~StreamsGuard() { for (int i = 0; i < 4; ++i) if (q[i]) cudaStreamDestroy(q[i]); }
+  } guard{cs};
+  COARSE_CUDA(cudaGraphCreate(&B.graph, 0));
+  BCtl hc{};
+  hc.max_ir = p->max_ir;
+  hc.max_cyc = p->max_restarts;
+  hc.steps_max = B.steps_max;
+  hc.tol = p->tol;
+  hc.inner_tol = p->inner_tol;
+  COARSE_CUDA(cudaGraphConditionalHandleCreate(&hc.h_ir, B.graph, 0, 0));
+  COARSE_CUDA(cudaGraphConditionalHandleCreate(&hc.h_cyc, B.graph, 0, 0));
+  COARSE_CUDA(cudaGraphConditionalHandleCreate(&hc.h_step, B.graph, 0, 0));
+  COARSE_CUDA(cudaMemcpyAsync(dctl, &hc, sizeof(BCtl), cudaMemcpyHostToDevice, s));
+  COARSE_CUDA(cudaStreamSynchronize(s));
+  cudaGraph_t body_ir = nullptr, body_cyc = nullptr, body_step = nullptr;
+  const bool zero_guess = (p->flags & COARSE_ZERO_GUESS) != 0;
+  auto step_body = [&](cudaStream_t q) -> int {
+    TRY(B.step_sequence(q));
+    kb_step_gate<<<1, kCtlThreads, 0, q>>>(dctl, B.dS, B.step, ns, 1);
+    note_launch();
+    COARSE_CUDA(cudaGetLastError());
+    return COARSE_OK;
+  };
+  auto cycle_body = [&](cudaStream_t q) -> int {
+    if (B.any_kc) {
+      TRY(B.vec(BV_PROJ_DOT, q));
+      TRY(B.vec(BV_PROJ_UPD, q));
+      TRY(B.elem(BE_COMBINE_U, q));
+      int src = BS_T;
+      TRY(B.precondition(BS_T, BG_ACTIVE, q, &src));
+      TRY(B.elem(BE_AXPY_E_PROJ, q, src, BG_ACTIVE));
     }
-    cudaStreamDestroy(cs);
+    TRY(B.vec(BV_NORM_R, q));
+    COARSE_CUDA(cudaMemsetAsync(B.step, 0, sizeof(int), q));
+    TRY(launch_bcycle_init(B.dS, ns, m, 0.0, q));
+    TRY(B.elem(BE_START, q, BS_ACC, BG_STEP));
+    kb_step_gate<<<1, kCtlThreads, 0, q>>>(dctl, B.dS, B.step, ns, 0);
+    note_launch();
+    COARSE_CUDA(cudaGetLastError());
+    TRY(add_while(q, hc.h_step, &body_step));
+    TRY(capture_body(body_step, cs[3], step_body));
+    TRY(launch_bcycle_solve(B.dS, ns, q));
+    TRY(B.elem(BE_COMBINE_T, q));
+    int src = BS_T;
+    TRY(B.precondition(BS_T, BG_TAIL, q, &src));
+    TRY(B.elem(BE_AXPY_E, q, src, BG_TAIL));
+    TRY(B.vec(BV_RES_UPD, q));
+    kb_cycle_end<<<1, kCtlThreads, 0, q>>>(dctl, B.dS, dinfo, ns);
+    note_launch();
+    COARSE_CUDA(cudaGetLastError());
+    return COARSE_OK;
+  };
+  auto ir_body = [&](cudaStream_t q) -> int {
+    kb_ir_begin<<<1, kCtlThreads, 0, q>>>(dctl, B.dS, dinfo, ns);
+    note_launch();
+    COARSE_CUDA(cudaGetLastError());
+    TRY(B.elem(BE_TO_LOW, q));
+    TRY(add_while(q, hc.h_cyc, &body_cyc));
+    TRY(capture_body(body_cyc, cs[2], cycle_body));
+    TRY(B.elem(BE_ADD_LOW, q));
+    TRY(B.residual64(q));
+    kb_ir_end<<<1, kCtlThreads, 0, q>>>(dctl, B.dS, dinfo, ns);
+    note_launch();
+    COARSE_CUDA(cudaGetLastError());
+    return COARSE_OK;
+  };
+  auto top = [&](cudaStream_t q) -> int {
+    if (zero_guess) TRY(B.elem(BE_ZERO_X, q));
+    TRY(B.residual64(q));
+    TRY(launch_bnorms64(B.dS, ns, B.chunk_off, B.total_chunks, B.E, 2, q));
+    kb_ctl_start<<<1, kCtlThreads, 0, q>>>(dctl, B.dS, dinfo, ns);
+    note_launch();
+    COARSE_CUDA(cudaGetLastError());
+    TRY(add_while(q, hc.h_ir, &body_ir));
+    return capture_body(body_ir, cs[1], ir_body);
+  };
+  const long long l_build0 = launches_so_far();
+  {
+    COARSE_CUDA(cudaStreamBeginCaptureToGraph(cs[0], B.graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int rc = top(cs[0]);
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs[0], &out);
+    if (rc == COARSE_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture (batched solve)");
     if (rc != COARSE_OK) return rc;
+    e = cudaGraphInstantiate(&B.gexec, B.graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batched solve)");
   }
-  size_t graph_nodes = 0;
-  cudaGraphGetNodes(B.graph, nullptr, &graph_nodes);
-
-  // ---- lockstep refinement
+  // the capture counted every kernel once; the graph's own accounting follows the replay below
+  note_launches(-(launches_so_far() - l_build0));
+  COARSE_CUDA(cudaGraphLaunch(B.gexec, s));
+  std::vector<BInfo> hinfo(ns);
+  BCtl ctl_h{};
+  COARSE_CUDA(cudaMemcpyAsync(hinfo.data(), dinfo, sizeof(BInfo) * ns, cudaMemcpyDeviceToHost, s));
+  COARSE_CUDA(cudaMemcpyAsync(&ctl_h, dctl, sizeof(BCtl), cudaMemcpyDeviceToHost, s));
+  COARSE_CUDA(cudaStreamSynchronize(s));
+  B.launches = (long long)graph_kernels(B.graph) + (long long)ctl_h.ir * (long long)graph_kernels(body_ir) +
+               (long long)ctl_h.cycles_run * (long long)graph_kernels(body_cyc) +
+               (long long)ctl_h.steps_run * (long long)graph_kernels(body_step);
   std::vector<coarse_solve_info> inf(ns);
   std::vector<double> bn(ns), rn(ns);
-  std::vector<int> done(ns, 0), active(ns, 0);
-  auto put_flags = [&]() -> int {
-    for (int q = 0; q < ns; ++q) {
-      B.flags_h[2 * q] = active[q];
-      B.flags_h[2 * q + 1] = done[q];
-    }
-    COARSE_CUDA(cudaMemcpyAsync(B.flags, B.flags_h, sizeof(int) * 2 * ns, cudaMemcpyHostToDevice, s));
-    return COARSE_OK;
-  };
-  auto get_norms = [&]() -> int {
-    COARSE_CUDA(cudaMemcpyAsync(B.norms_h, B.norms, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost, s));
-    COARSE_CUDA(cudaStreamSynchronize(s));
-    return COARSE_OK;
-  };
-  TRY(put_flags());
-  if (p->flags & COARSE_ZERO_GUESS) TRY(B.elem(BE_ZERO_X, s));
-  TRY(B.residual64(s));
-  TRY(launch_bnorms64(B.dS, ns, B.chunk_off, B.total_chunks, B.E, 2, s));
-  TRY(get_norms());
   bool any_nonfinite = false;
   for (int q = 0; q < ns; ++q) {
-    bn[q] = sqrt(B.norms_h[4 * q + 2]);
-    rn[q] = sqrt(B.norms_h[4 * q + 1]);
-    if (!isfinite(bn[q]) || !isfinite(rn[q])) {
-      inf[q].status = COARSE_ERR_NONFINITE;
-      done[q] = 1;
-      any_nonfinite = true;
-    } else {
-      done[q] = (bn[q] == 0.0 || rn[q] <= p->tol * bn[q]) ? 1 : 0;
-    }
-  }
-  for (int ir = 0; ir < p->max_ir; ++ir) {
-    int left = 0;
-    for (int q = 0; q < ns; ++q) left += !done[q];
-    if (left == 0) break;
-    for (int q = 0; q < ns; ++q) {
-      active[q] = !done[q];
-      B.norms_h[4 * q + 3] = std::max(p->inner_tol, 0.5 * p->tol * bn[q] / std::max(rn[q], 1e-300));
-    }
-    COARSE_CUDA(cudaMemcpyAsync(B.norms, B.norms_h, sizeof(double) * 4 * ns, cudaMemcpyHostToDevice, s));
-    TRY(put_flags());
-    TRY(B.elem(BE_TO_LOW, s));
-    for (int cyc = 0; cyc < p->max_restarts; ++cyc) {
-      int act = 0;
-      for (int q = 0; q < ns; ++q) act += active[q];
-      if (act == 0) break;
-      if (B.any_kc) {
-        TRY(B.vec(BV_PROJ_DOT, s));
-        TRY(B.vec(BV_PROJ_UPD, s));
-        TRY(B.elem(BE_COMBINE_U, s));
-        int src = BS_T;
-        TRY(B.precondition(BS_T, BG_ACTIVE, s, &src));
-        TRY(B.elem(BE_AXPY_E_PROJ, s, src, BG_ACTIVE));
-      }
-      TRY(B.vec(BV_NORM_R, s));
-      COARSE_CUDA(cudaMemsetAsync(B.step, 0, sizeof(int), s));
-      TRY(launch_bcycle_init(B.dS, ns, m, 0.0, s));
-      TRY(B.elem(BE_START, s, BS_ACC, BG_STEP));
-      // steps: graph replays in chunks of 4, stop flags read back one chunk behind
-      int pending = -1;
-      for (int j0 = 0; j0 < B.steps_max; j0 += 4) {
-        for (int j = j0; j < B.steps_max && j < j0 + 4; ++j) {
-          COARSE_CUDA(cudaGraphLaunch(B.gexec, s));
-          B.launches += (long long)graph_nodes;
-        }
-        const int slot = (j0 / 4) & 1;
-        COARSE_CUDA(cudaMemcpyAsync(B.states_h, B.states, sizeof(CycleState) * ns, cudaMemcpyDeviceToHost, s));
-        COARSE_CUDA(cudaEventRecord(B.ev[slot], s));
-        if (pending >= 0) {
-          COARSE_CUDA(cudaEventSynchronize(B.ev[pending]));
-          bool all = true;
-          for (int q = 0; q < ns && all; ++q) all = B.states_h[q].stop != 0;
-          if (all) break;
-        }
-        pending = slot;
-      }
-      COARSE_CUDA(cudaMemcpyAsync(B.states_h, B.states, sizeof(CycleState) * ns, cudaMemcpyDeviceToHost, s));
-      COARSE_CUDA(cudaStreamSynchronize(s));
-      std::vector<CycleState> cs(B.states_h, B.states_h + ns);
-      TRY(launch_bcycle_solve(B.dS, ns, s));
-      TRY(B.elem(BE_COMBINE_T, s));
-      int src = BS_T;
-      TRY(B.precondition(BS_T, BG_TAIL, s, &src));
-      TRY(B.elem(BE_AXPY_E, s, src, BG_TAIL));
-      TRY(B.vec(BV_RES_UPD, s));
-      for (int q = 0; q < ns; ++q) {
-        if (!active[q]) continue;
-        inf[q].cycles++;
-        inf[q].iterations += cs[q].j;
-        if (cs[q].status & ST_NONFINITE) {
-          inf[q].status = COARSE_ERR_NONFINITE;
-          done[q] = 1;
-          active[q] = 0;
-          any_nonfinite = true;
-          continue;
-        }
-        if (cs[q].j == 0 || cs[q].resid <= cs[q].target || (cs[q].status & (ST_LUCKY | ST_ZERO))) active[q] = 0;
-      }
-      TRY(put_flags());
-    }
-    TRY(B.elem(BE_ADD_LOW, s));
-    TRY(B.residual64(s));
-    TRY(get_norms());
-    for (int q = 0; q < ns; ++q) {
-      if (done[q]) continue;
-      inf[q].ir_steps++;
-      rn[q] = sqrt(B.norms_h[4 * q + 1]);
-      if (!isfinite(rn[q])) {
-        inf[q].status = COARSE_ERR_NONFINITE;
-        done[q] = 1;
-        any_nonfinite = true;
-      } else if (rn[q] <= p->tol * bn[q]) {
-        done[q] = 1;
-      }
-    }
+    inf[q].status = hinfo[q].status;
+    inf[q].iterations = hinfo[q].iterations;
+    inf[q].cycles = hinfo[q].cycles;
+    inf[q].ir_steps = hinfo[q].ir_steps;
+    bn[q] = hinfo[q].bn;
+    rn[q] = hinfo[q].rn;
+    any_nonfinite = any_nonfinite || hinfo[q].status == COARSE_ERR_NONFINITE;
   }
   COARSE_CUDA(cudaStreamSynchronize(s));
   const double total_ms = now_ms() - t0;
