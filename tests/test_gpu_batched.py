@@ -1,6 +1,6 @@
 """GPU parity of coarse_solve_batched: uneven operators (n = 16, 32, 48) with several
-right-hand sides each, advanced in lockstep (one launch per phase, the Arnoldi step as a
-CUDA graph).  Every column is checked against the FP64 oracle's direct solution and the
+right-hand sides each, advanced in lockstep (one launch per phase; the whole solve one CUDA
+graph whose conditional loops the device drives).  Every column is checked against the FP64 oracle's direct solution and the
 true FP64 residual is recomputed by the oracle.
 """
 import numpy as np
@@ -77,3 +77,40 @@ def test_batched_equals_single_operator_path(problems):
     assert rel(xb.cpu().numpy(), X) <= 1e-9
     d1.close()
     d2.close()
+
+
+def test_batched_bounds_and_statistics(problems):
+    """The batched solve is one graph whose loops the device ends: with max_ir = 1 and
+    max_restarts = 1 it stops after one cycle of at most m steps per solve and reports the
+    solves as not converged; a zero right-hand side is done before any step; the statistics of a
+    converged run (cycles, Arnoldi steps, refinement steps) are those of real work."""
+    from paper_2205_09104_gb300 import COARSE_ZERO_GUESS, CoarseOp, solve_batched, solve_params
+    ops, bs, xs = [], [], []
+    for op, mu, B, X, A in problems[:2]:
+        ops.append(CoarseOp(op.self_blocks.cuda(), op.hop_blocks.cuda(), op.dims, op.nv, mu=mu, precisions=(1, 2),
+                            max_nrhs=4))
+        b = torch.from_numpy(B).cuda().contiguous()
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    bs[1][0].zero_()   # a zero right-hand side
+    m = 6
+    p = solve_params(m=m, tol=1e-10, precision=1, poly_degree=2, defl_k=0, inner_tol=1e-5, max_restarts=1, max_ir=1,
+                     flags=COARSE_ZERO_GUESS)
+    infos = solve_batched(ops, bs, xs, p, allow_not_converged=True)
+    assert infos[2]["status"] == 0 and infos[2]["iterations"] == 0 and infos[2]["ir_steps"] == 0
+    for q in (0, 1, 3, 4):
+        assert infos[q]["status"] == -4, infos[q]
+        assert infos[q]["ir_steps"] == 1 and infos[q]["cycles"] == 1 and 1 <= infos[q]["iterations"] <= m
+        assert 0.0 < infos[q]["rel_residual"] < 1.0
+    for x in xs:
+        assert torch.isfinite(torch.view_as_real(x)).all()
+    p = solve_params(m=20, tol=1e-10, precision=1, poly_degree=4, defl_k=0, inner_tol=1e-5, max_restarts=50, max_ir=40,
+                     flags=COARSE_ZERO_GUESS)
+    infos = solve_batched(ops, bs, xs, p)
+    for q, inf in enumerate(infos):
+        if q == 2:
+            continue
+        assert inf["status"] == 0 and inf["ir_steps"] >= 2 and inf["cycles"] >= inf["ir_steps"]
+        assert inf["iterations"] >= inf["cycles"]
+    for o in ops:
+        o.close()
