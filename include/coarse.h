@@ -201,7 +201,9 @@ int coarse_residual_noalloc(const coarse_op* op, const void* b, const void* x, v
  * two streams; h_{i,i-1} = sqrt(||v^a||^2 - sum |h|^2 - sum |b|^2) replaces the second reduction,
  * and both recurrences (v, v^a) share the coefficients.  A negative value (loss of orthogonality)
  * is a breakdown: the cycle ends with the steps before it, the next cycle restarts from the
- * residual (coarse_solve_info.breakdowns counts them).  Every cycle of plain (pp-)GMRES is
+ * residual (coarse_solve_info.breakdowns counts them).  Orthogonality can also be lost while the
+ * value stays positive; a refinement step whose true FP64 residual did not decrease is undone
+ * and the solve continues with classical cycles (counted as a breakdown too).  Every cycle of plain (pp-)GMRES is
  * pipelined; GCRO-DR's first cycle, without a recycle space, stays the classical GMRES cycle, and
  * each pipelined GCRO-DR cycle needs the k products A c_j of the recycle vectors (computed once per
  * recycle space).  Costs m + 1 + 2k extra vectors of storage. */

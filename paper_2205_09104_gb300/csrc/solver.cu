@@ -493,7 +493,7 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
     const bool extract_full = full_first && kc == 0 && kdef > 0 && updates < ulimit;
     // pipelined cycles (Sec. 3.5): every cycle of pipelined GMRES; the cycles of GCRO-DR that have
     // a recycle space (its first cycle is the classical GMRES cycle)
-    p1_active = pipelined && (kdef == 0 || kc > 0);
+    p1_active = pipelined && !p1_off && (kdef == 0 || kc > 0);
     if (p1_active) {
       TRY(ensure_p1());
       if (kc > 0) TRY(ensure_vc(kc));
@@ -732,8 +732,13 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
   int rc = COARSE_OK;
   double rel = rn / bn;
   int stall = 0;
+  s->p1_off = false;
+  double2* xkeep = static_cast<double2*>(s->tmp64);  // x before a pipelined refinement step
   while (rel > p->tol && inf.ir_steps < p->max_ir) {
     InnerInfo ii;
+    const bool p1_step_now = s->pipelined && !s->p1_off;
+    if (p1_step_now)
+      COARSE_CUDA(cudaMemcpyAsync(xkeep, x64, sizeof(double2) * (size_t)N, cudaMemcpyDeviceToDevice, stream));
     COARSE_CUDA(cudaMemsetAsync(s->e, 0, (s->v64 ? sizeof(double2) : sizeof(float2)) * (size_t)N, stream));
     if (s->v64) {
       COARSE_CUDA(cudaMemcpyAsync(s->r, r64, sizeof(double2) * (size_t)N, cudaMemcpyDeviceToDevice, stream));
@@ -783,7 +788,22 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
     TRY(residual());
     COARSE_CUDA(cudaMemcpyAsync(hn, op->norms, sizeof(double), cudaMemcpyDeviceToHost, stream));
     COARSE_CUDA(cudaStreamSynchronize(stream));
-    const double rn_new = sqrt(hn[0]);
+    double rn_new = sqrt(hn[0]);
+    if (p1_step_now && !(rn_new < rn)) {
+      // Sec. 3.5: the pipelined recurrences can lose orthogonality without t turning negative;
+      // a refinement step that did not lower the true residual is undone, and this solve goes on
+      // with classical cycles (counted as a breakdown)
+      COARSE_CUDA(cudaMemcpyAsync(x64, xkeep, sizeof(double2) * (size_t)N, cudaMemcpyDeviceToDevice, stream));
+      TRY(residual());
+      COARSE_CUDA(cudaMemcpyAsync(hn, op->norms, sizeof(double), cudaMemcpyDeviceToHost, stream));
+      COARSE_CUDA(cudaStreamSynchronize(stream));
+      rn_new = sqrt(hn[0]);
+      s->p1_off = true;
+      inf.breakdowns++;
+      rn = rn_new;
+      rel = rn / bn;
+      continue;
+    }
     if (!isfinite(rn_new)) {
       set_error("non-finite residual during refinement");
       rc = COARSE_ERR_NONFINITE;

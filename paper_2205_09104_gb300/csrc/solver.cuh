@@ -81,6 +81,7 @@ struct Solver {
   // the stencil of the same step runs on `stream`.
   bool pipelined = false;
   bool p1_active = false;                // the current cycle is a pipelined one
+  bool p1_off = false;                   // this solve fell back to classical cycles
   void* p1mem = nullptr;
   std::vector<void*> Va;
   std::vector<void*> VC[2];
