@@ -183,8 +183,10 @@ int coarse_residual_noalloc(const coarse_op* op, const void* b, const void* x, v
  * S = 1 - D_ee^{-1} D_eo D_oo^{-1} D_oe over the even sites, with right-hand side
  * D_ee^{-1} (r_e - D_eo D_oo^{-1} r_o), and the odd sites are retrieved as
  * D_oo^{-1} (r_o - D_oe e_e); the FP64 refinement around it keeps the full operator.
- * Needs even lattice extents (COARSE_ERR_INVALID_ARG otherwise); FP64 solves and
- * coarse_solve_batched keep the full operator; coarse_solve_adjoint reduces the adjoint
+ * Needs even lattice extents (COARSE_ERR_INVALID_ARG otherwise); FP64 solves keep the full
+ * operator; coarse_solve_batched reduces every solve (all operators need even extents; the
+ * BF16 inner precision then uses the single-column stencil instead of the tensor-core
+ * multi-right-hand-side one); coarse_solve_adjoint reduces the adjoint
  * system sigma3 D_c(-mu) sigma3 the same way.  The first use (per sign of mu) computes the
  * inverses of the diagonal blocks A_x + i mu sigma3 in FP64. */
 #define COARSE_ODD_EVEN 0x20u

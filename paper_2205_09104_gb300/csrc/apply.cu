@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(128) kb_residual64(BApply b, const double2* co
   a.adjoint = 0;
   a.stop = nullptr;
   a.part = s.part64;
-  a.push = (char*)s.part64 + (size_t)s.N * sizeof(double2);
+  a.push = (char*)s.part64 + (size_t)s.Nf * sizeof(double2);
   a.cnt = s.cnt;
   a.err = s.cnt + s.V;
   apply_site<N, double2, double2, double2>(a, g - b.site_off[k], ys[warp]);

@@ -52,10 +52,25 @@ struct BSolve {
   double* norm2;       // [0] ||r||^2 (inner), [1] ||r64||^2, [2] ||b||^2
   int* flags;          // [0] inner-active this cycle, [1] done (tolerance met)
   int nch;             // CTAs of this solve in the chunked reductions
+  // odd-even reduction (COARSE_ODD_EVEN): the Krylov vectors above are the even halves (N = V n / 2);
+  // the FP64 refinement keeps full-length vectors (Nf = V n, nchf chunks)
+  int eo;
+  int Nf, nchf;
+  const void* inv;      // inverses of the diagonal blocks in the inner precision [V][n][n]
+  const void* inv_poly; // the same in the precision of the polynomial-chain phases
+  const int4* eo_rec;   // neighbour records (coarse_op::eo_rec)
+  const int* eo_sites;  // even sites, then odd sites, increasing (coarse_op::eo_sites)
+  void* f32;            // full-length FP32 work vector (residual in, correction out)
+  void* re;             // even / odd halves of the residual
+  void* ro;
+  void* to;             // D_oo^{-1} r_o
+  void* eoe;            // odd part of the correction
+  void* todd;           // odd intermediate of an S apply
 };
 
 // Which vector a batched stencil phase reads / writes.
-enum BSel : int { BS_VJ = 0, BS_VJ1, BS_SA, BS_SB, BS_ACC, BS_T, BS_R };
+enum BSel : int { BS_NONE = -1, BS_VJ = 0, BS_VJ1, BS_SA, BS_SB, BS_ACC, BS_T, BS_R, BS_E, BS_TODD, BS_RE, BS_RO,
+                  BS_TO, BS_EOE };
 
 // Gate of a batched phase: run the solve's part only if ...
 enum BGate : int {
@@ -108,9 +123,33 @@ __device__ inline void* bsel(const BSolve& s, int sel, int step) {
     case BS_ACC: return s.acc;
     case BS_T: return s.t;
     case BS_R: return s.r;
+    case BS_E: return s.e;
+    case BS_TODD: return s.todd;
+    case BS_RE: return s.re;
+    case BS_RO: return s.ro;
+    case BS_TO: return s.to;
+    case BS_EOE: return s.eoe;
   }
   return nullptr;
 }
+
+// One batched half apply of the odd-even reduced operator (Sec. 2, Sec. 3.2) over an n-group:
+// output sites of parity out_par, y = B^{-1} (z - sum hops v) or base - B^{-1} (...), chain epilogue.
+struct BEoApply {
+  const BSolve* S;
+  const int* sidx;      // solves of this n-group
+  const int* site_off;  // prefix sums of their half-site counts V / 2 (count + 1 entries)
+  int count;
+  int total;            // total output sites
+  int out_par;
+  int vsel, zsel, bsel, ysel;  // BSel (BS_NONE: absent)
+  int mode;
+  int coef_off;
+  int gate;
+  const int* step;
+  int poly_blocks;      // 1: the chain's blocks and inverses
+};
+int launch_beo_half(int prec, int n, const BEoApply& b, cudaStream_t s);
 
 int launch_bapply(int prec, int n, const BApply& a, cudaStream_t s);
 
@@ -168,7 +207,17 @@ enum BElem : int {
   BE_TO_LOW,         // r = r64 / ||r64||, e = 0                (gate not done)
   BE_ADD_LOW,        // x64 += ||r64|| e                        (gate not done)
   BE_ZERO_X,         // x64 = 0                                 (all)
+  // odd-even reduction (Sec. 2): the refinement's residual and correction through the halves
+  BE_TO_LOW_F,       // f32 = r64 / ||r64||                     (gate not done, full length)
+  BE_EO_SPLIT,       // re, ro = even / odd parts of f32, e = 0 (gate not done, half length)
+  BE_EO_MERGE,       // f32 = (e on the even sites, eoe on the odd sites) (gate not done, half length)
+  BE_ADD_LOW_F,      // x64 += ||r64|| f32                      (gate not done, full length)
 };
+// Phases over the full-length vectors (launched with the full-length chunk table): the FP64
+// refinement's and those that read or write r64, x64 or f32.
+__host__ __device__ inline bool belem_full(int op) {
+  return op == BE_TO_LOW || op == BE_ADD_LOW || op == BE_ZERO_X || op == BE_TO_LOW_F || op == BE_ADD_LOW_F;
+}
 // aux: source of BE_AXPY_E (BS_ACC or BS_T); gate: BGate of BE_AXPY_E
 int launch_belem(int op, const BSolve* S, int nsolves, const int* chunk_off, int total_chunks, int E,
                  const int* step, int aux, int gate, cudaStream_t s);

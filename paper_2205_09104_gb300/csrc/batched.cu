@@ -18,6 +18,7 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "mrhs_core.cuh"
+#include "oddeven.cuh"
 #include "solver.cuh"
 
 namespace coarse {
@@ -73,6 +74,12 @@ struct Batch {
   double* norms = nullptr;
   int* flags = nullptr;
   int* chunk_off = nullptr;
+  // odd-even reduction: the Krylov phases run on the even halves (chunk_off, total_chunks), the
+  // refinement's full-length phases on chunk_off_f / total_chunks_f; egroups: half-site groups
+  bool eo = false;
+  int* chunk_off_f = nullptr;
+  int total_chunks_f = 0;
+  std::vector<Group> egroups;
   std::vector<Group> groups;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -84,8 +91,38 @@ struct Batch {
     if (mem) cudaFree(mem);
   }
 
+  // one half apply of the odd-even reduced operator over every n-group
+  int eo_half(int out_par, int vsel, int zsel, int bsel, int ysel, int mode, int coef_off, int gate, bool chain,
+              cudaStream_t s) {
+    for (const Group& g : egroups) {
+      BEoApply a;
+      a.S = dS;
+      a.sidx = g.sidx;
+      a.site_off = g.site_off;
+      a.count = g.count;
+      a.total = g.total;
+      a.out_par = out_par;
+      a.vsel = vsel;
+      a.zsel = zsel;
+      a.bsel = bsel;
+      a.ysel = ysel;
+      a.mode = mode;
+      a.coef_off = coef_off;
+      a.gate = gate;
+      a.step = step;
+      a.poly_blocks = chain ? 1 : 0;
+      TRY(launch_beo_half(chain ? poly_prec : prec, g.n, a, s));
+    }
+    return COARSE_OK;
+  }
+
   // one stencil phase over all n-groups (chain: a polynomial-chain phase, on the chain's blocks)
   int apply_phase(int mode, int xsel, int ysel, int coef_off, int gate, cudaStream_t s, bool chain = false) {
+    if (eo) {
+      // y = S x: t_o = B_o^{-1} D_oe x, then y = x - B_e^{-1} D_eo t_o with the chain epilogue
+      TRY(eo_half(1, xsel, BS_NONE, BS_NONE, BS_TODD, APPLY_PLAIN, 0, gate, chain, s));
+      return eo_half(0, BS_TODD, BS_NONE, xsel, ysel, mode, coef_off, gate, chain, s);
+    }
     if (mrhs) {
       for (size_t i = 0; i < mgroups.size(); ++i) {
         BMApply a = mgroups[i].a;
@@ -135,7 +172,25 @@ struct Batch {
 
   int vec(int op, cudaStream_t s) { return launch_bvec(op, dS, ns, chunk_off, total_chunks, E, step, s); }
   int elem(int op, cudaStream_t s, int aux = BS_ACC, int gate = BG_TAIL) {
+    if (belem_full(op)) return launch_belem(op, dS, ns, chunk_off_f, total_chunks_f, E, step, aux, gate, s);
     return launch_belem(op, dS, ns, chunk_off, total_chunks, E, step, aux, gate, s);
+  }
+  int norms64(int which, cudaStream_t s) {
+    return launch_bnorms64(dS, ns, chunk_off_f, total_chunks_f, E, which, s);
+  }
+
+  // refinement step, odd-even: the reduced right-hand side r = B_e^{-1} (r_e - D_eo D_oo^{-1} r_o)
+  // from the full residual, and afterwards the full correction from e (Sec. 2, Sec. 3.2)
+  int eo_rhs(cudaStream_t s) {
+    TRY(elem(BE_TO_LOW_F, s));
+    TRY(elem(BE_EO_SPLIT, s));
+    TRY(eo_half(1, BS_NONE, BS_RO, BS_NONE, BS_TO, APPLY_PLAIN, 0, BG_NOTDONE, false, s));
+    return eo_half(0, BS_TO, BS_RE, BS_NONE, BS_R, APPLY_PLAIN, 0, BG_NOTDONE, false, s);
+  }
+  int eo_correction(cudaStream_t s) {
+    TRY(eo_half(1, BS_E, BS_NONE, BS_TO, BS_EOE, APPLY_PLAIN, 0, BG_NOTDONE, false, s));
+    TRY(elem(BE_EO_MERGE, s));
+    return elem(BE_ADD_LOW_F, s);
   }
 
   // one Arnoldi step of every running solve: A v_j -> CGS2 -> finalize -> normalise -> step++
@@ -167,7 +222,7 @@ struct Batch {
       a.poly_blocks = 0;
       TRY(launch_bapply64_residual(g.n, a, s));
     }
-    return launch_bnorms64(dS, ns, chunk_off, total_chunks, E, 1, s);
+    return norms64(1, s);
   }
 };
 
@@ -388,6 +443,14 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   const int prec = p->precision;
   const int m = p->m, k = p->defl_k, d = p->poly_degree;
   const long long launches0 = launches_so_far();
+  // COARSE_ODD_EVEN: every solve's inner system is the block-Jacobi preconditioned reduced S
+  const bool eo = (p->flags & COARSE_ODD_EVEN) != 0;
+  if (eo)
+    for (int i = 0; i < nops; ++i)
+      if (!ops[i]->eo_sites) {
+        set_error("coarse_solve_batched: COARSE_ODD_EVEN needs even lattice extents (operator %d)", i);
+        return COARSE_ERR_INVALID_ARG;
+      }
 
   // ---- setup per operator: polynomial and recycle space through the single-operator solver
   double setup_ms = 0.0;
@@ -417,8 +480,9 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
         rc = COARSE_ERR_INVALID_ARG;
         break;
       }
-      Solver* sv = get_solver(op, prec, 0, s);
+      Solver* sv = get_solver(op, prec, 0, s, eo ? 1 : 0);
       const int N = op->V * op->n;
+      if (eo && (rc = eo_prepare(op, op->mu, s)) != COARSE_OK) break;
       if ((rc = sv->ensure(m, k, d > 0 ? d : 1)) != COARSE_OK) break;
       if (!sv->poly_ok || (d > 0 && sv->d == 0) || (d == 0 && sv->d != 0)) {
         if ((rc = sv->build_poly(nullptr, p->seed + i, d)) != COARSE_OK) break;  // seeded start per operator
@@ -454,8 +518,8 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   const int maxq = kMaxK + kMaxDense + 2;
   const int ldh = kMaxDense + 1;
   std::vector<size_t> off_vec(ns), off_small(ns);
-  std::vector<int> nch(ns);
-  std::vector<int> chunk_off(ns + 1, 0);
+  std::vector<int> nch(ns), nchf(ns);
+  std::vector<int> chunk_off(ns + 1, 0), chunk_off_f(ns + 1, 0);
   size_t bytes = 0;
   auto take = [&](size_t n) { size_t o = bytes; bytes += align256(n); return o; };
   const size_t o_step = take(64);
@@ -464,12 +528,15 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   const size_t o_flags = take(sizeof(int) * 2 * ns);
   const size_t o_S = take(sizeof(BSolve) * ns);
   const size_t o_coff = take(sizeof(int) * (ns + 1));
+  const size_t o_coff_f = take(sizeof(int) * (ns + 1));
   const size_t o_groups = take(sizeof(int) * (2 * ns + 8) * 3);
+  const size_t o_egroups = take(sizeof(int) * (2 * ns + 8) * 3);
   const size_t o_ctl = take(sizeof(BCtl));
   const size_t o_info = take(sizeof(BInfo) * ns);
   // multi-RHS stencil phases: BF16 inner solves, every operator carrying the fragment-layout
   // blocks (created with max_nrhs > 1) and at most 12 columns
-  B.mrhs = prec == COARSE_PREC_BF16;
+  B.eo = eo;
+  B.mrhs = prec == COARSE_PREC_BF16 && !eo;
   for (int i = 0; i < nops; ++i) B.mrhs = B.mrhs && ops[i]->mrhs.ptr != nullptr && nrhs[i] <= kMrhsColumns;
   std::vector<size_t> off_xb(nops, 0);
   size_t o_mops = 0, o_mgrp = 0, o_woff = 0, o_merr = 0;
@@ -492,21 +559,24 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
     for (int i = 0; i < nops; ++i) {
       const int N = ops[i]->V * ops[i]->n;
       const int V = ops[i]->V;
-      Solver* sv = ops[i]->solver[prec];
+      Solver* sv = eo ? ops[i]->eo_solver[prec] : ops[i]->solver[prec];
       const int kc = sv->k_cur;
       for (int c = 0; c < nrhs[i]; ++c, ++sidx) {
-        nch[sidx] = batch_chunks(N, B.E);
+        nch[sidx] = batch_chunks(eo ? N / 2 : N, B.E);
+        nchf[sidx] = batch_chunks(N, B.E);
         chunk_off[sidx + 1] = chunk_off[sidx] + nch[sidx];
+        chunk_off_f[sidx + 1] = chunk_off_f[sidx] + nchf[sidx];
         off_vec[sidx] = take(sizeof(float2) * (size_t)N * (m + 7) + sizeof(float2) * 5 * (size_t)N +
                              sizeof(double2) * 6 * (size_t)N + sizeof(int) * (V + 4) + 1024);
         off_small[sidx] = take(sizeof(double2) * (2 * (size_t)ldh * kMaxDense + 3 * kMaxDense + (size_t)kMaxK * kMaxDense +
                                                   4 * maxq + 3 * kMaxPoly + 4) +
-                               sizeof(double) * 2 * (size_t)kBatchMaxQ * nch[sidx] + sizeof(void*) * (3 * (kc + m + 2)) +
+                               sizeof(double) * 2 * (size_t)kBatchMaxQ * nchf[sidx] + sizeof(void*) * (3 * (kc + m + 2)) +
                                4096);
       }
     }
   }
   B.total_chunks = chunk_off[ns];
+  B.total_chunks_f = chunk_off_f[ns];
   if (cudaMalloc((void**)&B.mem, bytes) != cudaSuccess) {
     cudaGetLastError();
     set_error("coarse_solve_batched: allocation of %zu bytes failed", bytes);
@@ -519,10 +589,12 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   B.flags = reinterpret_cast<int*>(B.mem + o_flags);
   B.dS = reinterpret_cast<BSolve*>(B.mem + o_S);
   B.chunk_off = reinterpret_cast<int*>(B.mem + o_coff);
+  B.chunk_off_f = reinterpret_cast<int*>(B.mem + o_coff_f);
   {
     const double2 cst[2] = {make_double2(-1.0, 0.0), make_double2(1.0, 0.0)};
     COARSE_CUDA(cudaMemcpyAsync(B.step + 4, cst, sizeof(cst), cudaMemcpyHostToDevice, s));
     COARSE_CUDA(cudaMemcpyAsync(B.chunk_off, chunk_off.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice, s));
+    COARSE_CUDA(cudaMemcpyAsync(B.chunk_off_f, chunk_off_f.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice, s));
   }
   std::vector<BSolve> hs(ns);
   std::vector<std::vector<void*>> tabs(ns);
@@ -531,7 +603,7 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
     int sidx = 0;
     for (int i = 0; i < nops; ++i) {
       coarse_op* op = ops[i];
-      Solver* sv = op->solver[prec];
+      Solver* sv = eo ? op->eo_solver[prec] : op->solver[prec];
       const int N = op->V * op->n;
       const int kc = sv->k_cur;
       B.any_kc = B.any_kc || kc > 0;
@@ -565,7 +637,9 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
         S.nb = op->nb;
         S.V = op->V;
         S.n = op->n;
-        S.N = N;
+        S.N = eo ? N / 2 : N;
+        S.Nf = N;
+        S.eo = eo ? 1 : 0;
         S.kc = kc;
         S.mu = op->mu;
         std::vector<void*>& T = tabs[sidx];
@@ -578,6 +652,21 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
         S.acc = v + (m + 6) * vb;
         S.part = v + (m + 7) * vb;
         S.push = v + (m + 8) * vb;
+        if (eo) {
+          // the half apply keeps no stencil scratch: its 5 N-vector region holds the odd-even work
+          const size_t hb = vb / 2;
+          char* w = v + (m + 7) * vb;
+          S.f32 = w;
+          S.re = w + vb;
+          S.ro = w + vb + hb;
+          S.to = w + vb + 2 * hb;
+          S.eoe = w + vb + 3 * hb;
+          S.todd = w + vb + 4 * hb;
+          S.inv = op->inv[0][prec].ptr;
+          S.inv_poly = op->inv[0][B.poly_prec].ptr;
+          S.eo_rec = op->eo_rec;
+          S.eo_sites = op->eo_sites;
+        }
         char* v64 = v + (m + 12) * vb;
         S.r64 = reinterpret_cast<double2*>(v64);
         S.part64 = v64 + sizeof(double2) * (size_t)N;
@@ -615,6 +704,7 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
         S.norm2 = B.norms + 4 * sidx;
         S.flags = B.flags + 2 * sidx;
         S.nch = nch[sidx];
+        S.nchf = nchf[sidx];
         // pointer tables: vt = basis, qt = [C, basis], ut = [U, basis]
         std::vector<void*> hq, hu;
         for (int j = 0; j < kc; ++j) hq.push_back(sv->C[sv->par][j]);
@@ -720,6 +810,29 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
       B.groups.push_back(g);
     }
   }
+  // odd-even: n-groups over the half-site counts (one output parity per half apply)
+  if (eo) {
+    int* g0 = reinterpret_cast<int*>(B.mem + o_egroups);
+    for (int n : {16, 32, 48}) {
+      std::vector<int> idx, off(1, 0);
+      for (int q = 0; q < ns; ++q)
+        if (hs[q].n == n) {
+          idx.push_back(q);
+          off.push_back(off.back() + hs[q].V / 2);
+        }
+      if (idx.empty()) continue;
+      Group g;
+      g.n = n;
+      g.count = (int)idx.size();
+      g.total = off.back();
+      g.sidx = g0;
+      g.site_off = g0 + idx.size();
+      COARSE_CUDA(cudaMemcpyAsync(g.sidx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
+      COARSE_CUDA(cudaMemcpyAsync(g.site_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
+      g0 += idx.size() + off.size();
+      B.egroups.push_back(g);
+    }
+  }
   int kmin = m;
   for (int q = 0; q < ns; ++q) kmin = std::min(kmin, hs[q].kc);
   B.steps_max = kmin > 0 ? m - kmin : m;
@@ -788,10 +901,12 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
     kb_ir_begin<<<1, kCtlThreads, 0, q>>>(dctl, B.dS, dinfo, ns);
     note_launch();
     COARSE_CUDA(cudaGetLastError());
-    TRY(B.elem(BE_TO_LOW, q));
+    if (eo) TRY(B.eo_rhs(q));
+    else TRY(B.elem(BE_TO_LOW, q));
     TRY(add_while(q, hc.h_cyc, &body_cyc));
     TRY(capture_body(body_cyc, cs[2], cycle_body));
-    TRY(B.elem(BE_ADD_LOW, q));
+    if (eo) TRY(B.eo_correction(q));
+    else TRY(B.elem(BE_ADD_LOW, q));
     TRY(B.residual64(q));
     kb_ir_end<<<1, kCtlThreads, 0, q>>>(dctl, B.dS, dinfo, ns);
     note_launch();
@@ -801,7 +916,7 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   auto top = [&](cudaStream_t q) -> int {
     if (zero_guess) TRY(B.elem(BE_ZERO_X, q));
     TRY(B.residual64(q));
-    TRY(launch_bnorms64(B.dS, ns, B.chunk_off, B.total_chunks, B.E, 2, q));
+    TRY(B.norms64(2, q));
     kb_ctl_start<<<1, kCtlThreads, 0, q>>>(dctl, B.dS, dinfo, ns);
     note_launch();
     COARSE_CUDA(cudaGetLastError());
@@ -858,7 +973,7 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
   {
     int q = 0;
     for (int i = 0; i < nops; ++i) {
-      Solver* sv = ops[i]->solver[prec];
+      Solver* sv = eo ? ops[i]->eo_solver[prec] : ops[i]->solver[prec];
       for (int c = 0; c < nrhs[i]; ++c, ++q) inf[q].recycle_updates = sv->updates;
     }
   }

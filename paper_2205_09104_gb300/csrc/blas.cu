@@ -520,11 +520,13 @@ __global__ void __launch_bounds__(32 * kW) kb_elem(int op, const BSolve* S, int 
     case BE_COMBINE_U: run = bgate(s, BG_ACTIVE) && s.kc > 0; break;
     case BE_AXPY_E: run = bgate(s, gate); break;
     case BE_AXPY_E_PROJ: run = bgate(s, BG_ACTIVE) && s.kc > 0; break;
-    case BE_TO_LOW: case BE_ADD_LOW: run = bgate(s, BG_NOTDONE); break;
+    case BE_TO_LOW: case BE_ADD_LOW: case BE_TO_LOW_F: case BE_EO_SPLIT: case BE_EO_MERGE: case BE_ADD_LOW_F:
+      run = bgate(s, BG_NOTDONE);
+      break;
     default: run = true; break;
   }
   if (!run) return;
-  const int N = s.N;
+  const int N = belem_full(op) ? s.Nf : s.N;
   int nin = 0;
   const float2* const* in = nullptr;
   if (op == BE_COMBINE_T || op == BE_COMBINE_U) {
@@ -567,12 +569,32 @@ __global__ void __launch_bounds__(32 * kW) kb_elem(int op, const BSolve* S, int 
         ((float2*)s.r)[idx] = make_float2(float(a.x * inv), float(a.y * inv));
         ((float2*)s.e)[idx] = make_float2(0.f, 0.f);
       } break;
-      case BE_ADD_LOW: {
-        const float2 d = ((const float2*)s.e)[idx];
+      case BE_ADD_LOW:
+      case BE_ADD_LOW_F: {
+        const float2 d = ((const float2*)(op == BE_ADD_LOW ? s.e : s.f32))[idx];
         double2 x = s.x64[idx];
         x.x = fma(rn, double(d.x), x.x);
         x.y = fma(rn, double(d.y), x.y);
         s.x64[idx] = x;
+      } break;
+      case BE_TO_LOW_F: {
+        const double2 a = s.r64[idx];
+        const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+        ((float2*)s.f32)[idx] = make_float2(float(a.x * inv), float(a.y * inv));
+      } break;
+      case BE_EO_SPLIT: {
+        // idx runs over the half vectors: site k of each parity, component c
+        const int k = (int)(idx / s.n), c = (int)(idx % s.n);
+        const float2* f = (const float2*)s.f32;
+        ((float2*)s.re)[idx] = f[(size_t)s.eo_sites[k] * s.n + c];
+        ((float2*)s.ro)[idx] = f[(size_t)s.eo_sites[s.V / 2 + k] * s.n + c];
+        ((float2*)s.e)[idx] = make_float2(0.f, 0.f);
+      } break;
+      case BE_EO_MERGE: {
+        const int k = (int)(idx / s.n), c = (int)(idx % s.n);
+        float2* f = (float2*)s.f32;
+        f[(size_t)s.eo_sites[k] * s.n + c] = ((const float2*)s.e)[idx];
+        f[(size_t)s.eo_sites[s.V / 2 + k] * s.n + c] = ((const float2*)s.eoe)[idx];
       } break;
       default: s.x64[idx] = make_double2(0.0, 0.0); break;
     }
@@ -594,12 +616,12 @@ __global__ void __launch_bounds__(32 * kW) kb_norm64(const BSolve* S, int nsolve
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const long long idx = base + lane + 32 * e;
-    if (idx < s.N) { const double2 a = v[idx]; nn += a.x * a.x + a.y * a.y; }
+    if (idx < s.Nf) { const double2 a = v[idx]; nn += a.x * a.x + a.y * a.y; }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
   if (lane == 0) wp[warp * kMaxQ] = make_double2(nn, 0.0);
-  cta_finish(wp, 1, s.partial, s.counter, nullptr, s.norm2 + which, 0, cta, s.nch);
+  cta_finish(wp, 1, s.partial, s.counter, nullptr, s.norm2 + which, 0, cta, s.nchf);
 }
 
 }  // namespace

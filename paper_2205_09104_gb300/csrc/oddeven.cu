@@ -17,6 +17,7 @@
 
 #include "apply_core.cuh"
 #include "common.cuh"
+#include "batch.cuh"
 #include "oddeven.cuh"
 #include "pipe.cuh"
 #include "tune.cuh"
@@ -158,8 +159,10 @@ template <int N, class AC, int W, bool PF>
 constexpr int eo_min_blocks() {
   return (PF && W == 2 && N == 32 && sizeof(decltype(AC{}.x)) == 4) ? 14 : 0;
 }
-template <int N, class BT, class VT, class AC, int W, bool UNROLL = false, bool PF = false>
-__global__ void __launch_bounds__(32 * W, eo_min_blocks<N, AC, W, PF>()) k_eo_half(EoArgs a) {
+// One output site k of a half apply (the CTA's W warps together); shared by the single-operator
+// kernel below and the batched one (one CTA per (solve, site)).
+template <int N, class BT, class VT, class AC, int W, bool UNROLL, bool PF>
+__device__ __forceinline__ void eo_half_site(const EoArgs& a, const int k) {
   constexpr int CPL = N / 8, KR = N / 4, NV = N / 2, KW = KR / W;  // KW row quads per warp
   constexpr size_t BSZ = (size_t)N * N;
   using AT = decltype(AC{}.x);
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(32 * W, eo_min_blocks<N, AC, W, PF>()) k_eo_ha
   __shared__ __align__(8) uint64_t sbar;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 3, t = lane & 7;
-  const int k = blockIdx.x, nh = a.V / 2;
+  const int nh = a.V / 2;
   if (k >= nh) return;  // CTA-uniform
   const int4* rp = a.rec + ((size_t)a.out_par * nh + k) * 4;
   int4 rc[4];
@@ -352,6 +355,39 @@ __global__ void __launch_bounds__(32 * W, eo_min_blocks<N, AC, W, PF>()) k_eo_ha
       *accp = ao;
     }
   }
+}
+
+template <int N, class BT, class VT, class AC, int W, bool UNROLL = false, bool PF = false>
+__global__ void __launch_bounds__(32 * W, eo_min_blocks<N, AC, W, PF>()) k_eo_half(EoArgs a) {
+  eo_half_site<N, BT, VT, AC, W, UNROLL, PF>(a, blockIdx.x);
+}
+
+// Batched half apply: CTA g of the flat grid takes output site g of the n-group (half-site prefix
+// sums give its solve), builds that solve's arguments and runs the two-warp unrolled layout.
+template <int N, class BT>
+__global__ void __launch_bounds__(64) kb_eo_half(BEoApply b) {
+  const int g = blockIdx.x;
+  if (g >= b.total) return;
+  const int k = find_solve(b.site_off, b.count, g);
+  const BSolve& s = b.S[b.sidx[k]];
+  if (!bgate(s, b.gate)) return;  // uniform for all sites of the solve
+  const int step = *b.step;
+  EoArgs a{};
+  a.blocks = b.poly_blocks ? s.blk_poly : s.blk;
+  a.inv = b.poly_blocks ? s.inv_poly : s.inv;
+  a.rec = s.eo_rec;
+  a.err = s.cnt + s.V;
+  a.V = s.V;
+  a.out_par = b.out_par;
+  a.v = bsel(s, b.vsel, step);
+  a.z = bsel(s, b.zsel, step);
+  a.base = bsel(s, b.bsel, step);
+  a.y = bsel(s, b.ysel, step);
+  a.mode = b.mode;
+  a.acc = s.acc;
+  a.coef = s.polyc + b.coef_off;
+  a.stop = nullptr;
+  eo_half_site<N, BT, float2, float2, 2, true, false>(a, g - b.site_off[k]);
 }
 
 // Warp-per-site variant (4 sites per CTA): one warp walks all 9 blocks of its site.
@@ -1084,6 +1120,24 @@ int launch_eo_merge(int v64, const void* ev, const void* od, const int* sites, i
 
 // y = S x on compressed even vectors (t: odd scratch of the vector type), with an optional
 // polynomial-chain epilogue (mode, acc, coef) as the full stencil's.
+int launch_beo_half(int prec, int n, const BEoApply& b, cudaStream_t s) {
+  if (b.total <= 0) return COARSE_OK;
+  const dim3 grid(b.total);
+#define BEO(NN)                                                                              \
+  if (prec == COARSE_PREC_BF16) kb_eo_half<NN, cbf16><<<grid, 64, 0, s>>>(b);                \
+  else kb_eo_half<NN, float2><<<grid, 64, 0, s>>>(b);
+  switch (n) {
+    case 16: BEO(16) break;
+    case 32: BEO(32) break;
+    case 48: BEO(48) break;
+    default: set_error("batched odd-even: unsupported n = %d", n); return COARSE_ERR_INVALID_ARG;
+  }
+#undef BEO
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return COARSE_OK;
+}
+
 int launch_eo_schur(const coarse_op* op, int prec, double mu_eff, const void* x, void* y, void* t, int mode, void* acc,
                     const double2* coef, const int* stop, cudaStream_t s) {
   EoArgs a{};

@@ -527,6 +527,14 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
     matvecs -= (long long)(launched - cs.j) * (d > 1 ? d : 1);  // gated steps did not run
     info->cycles++;
     if (cs.status & ST_NONFINITE) {
+      if (p1_active) {
+        // Sec. 3.5: the pipelined recurrences never renormalise v^a; after a loss of orthogonality
+        // they can grow without bound.  The cycle is dropped (r and e untouched) and the solve goes
+        // on with classical cycles, counted as a breakdown.
+        info->breakdowns++;
+        p1_off = true;
+        continue;
+      }
       set_error("non-finite value in the Arnoldi process");
       return COARSE_ERR_NONFINITE;
     }

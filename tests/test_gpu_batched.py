@@ -114,3 +114,69 @@ def test_batched_bounds_and_statistics(problems):
         assert inf["iterations"] >= inf["cycles"]
     for o in ops:
         o.close()
+
+
+EO_CASES = [  # even coarse extents: key, fine dims, nv, mu, nrhs
+    ((810, 0), (4, 4, 4, 4), 8, 0.0, 2),
+    ((811, 0), (8, 4, 4, 8), 16, 0.0, 3),
+    ((812, 0), (4, 8, 4, 4), 24, 0.01, 1),
+    ((813, 0), (8, 8, 8, 8), 8, 0.02, 2),
+]
+
+
+@pytest.fixture(scope="module")
+def eo_problems():
+    out = []
+    for key, fdims, nv, mu, nr in EO_CASES:
+        op = make_op(key, fdims, nv, m0=-0.4)
+        N = op.volume * op.n
+        B = rhs((*key, 5), nr, N)
+        A = ocoarse.assemble(op.self_blocks.numpy(), op.hop_blocks.numpy(), op.dims, mu).tocsc()
+        lu = spla.splu(A)
+        X = np.stack([lu.solve(B[c]) for c in range(nr)])
+        out.append((op, mu, B, X, A))
+    return out
+
+
+@pytest.mark.parametrize("prec,chain_bf16,k", [(1, False, 4), (1, True, 4), (2, False, 0), (1, True, 0)])
+def test_batched_odd_even_matches_oracle(eo_problems, prec, chain_bf16, k):
+    """COARSE_ODD_EVEN in the batched engine (Sec. 2, Sec. 3.2): every solve's inner system is the
+    block-Jacobi preconditioned reduced S on the even sites, the odd sites retrieved per
+    refinement step; every column against the oracle's direct solution of the full system."""
+    from paper_2205_09104_gb300 import (COARSE_ODD_EVEN, COARSE_POLY_BF16, COARSE_ZERO_GUESS, CoarseOp, solve_batched,
+                                        solve_params)
+    ops, bs, xs = [], [], []
+    for op, mu, B, X, A in eo_problems:
+        ops.append(CoarseOp(op.self_blocks.cuda(), op.hop_blocks.cuda(), op.dims, op.nv, mu=mu, precisions=(1, 2),
+                            max_nrhs=4))
+        bs.append(torch.from_numpy(B).cuda().contiguous())
+        xs.append(torch.zeros_like(bs[-1]))
+    p = solve_params(m=20, tol=1e-10, precision=prec, poly_degree=4, defl_k=k, recycle_updates=10,
+                     inner_tol=1e-5 if prec == 1 else 1e-2, max_restarts=50, max_ir=40,
+                     flags=COARSE_ZERO_GUESS | COARSE_ODD_EVEN | (COARSE_POLY_BF16 if chain_bf16 else 0))
+    infos = solve_batched(ops, bs, xs, p)
+    q = 0
+    for (op, mu, B, X, A), x in zip(eo_problems, xs):
+        xg = x.cpu().numpy()
+        for c in range(B.shape[0]):
+            res = np.linalg.norm(B[c] - A @ xg[c]) / np.linalg.norm(B[c])
+            assert res <= 1e-10, (q, res, infos[q])
+            assert rel(xg[c], X[c]) <= 1e-9, (q, infos[q])
+            assert infos[q]["status"] == 0
+            assert abs(infos[q]["rel_residual"] - res) <= 1e-6 * max(res, 1e-12) + 1e-13
+            q += 1
+    for o in ops:
+        o.close()
+
+
+def test_batched_odd_even_rejects_odd_extents(problems):
+    from paper_2205_09104_gb300 import COARSE_ODD_EVEN, COARSE_ZERO_GUESS, CoarseError, CoarseOp, solve_batched, solve_params
+    op, mu, B, X, A = problems[1]                      # coarse 3x2x2x3
+    dev = CoarseOp(op.self_blocks.cuda(), op.hop_blocks.cuda(), op.dims, op.nv, mu=mu, max_nrhs=4)
+    b = torch.from_numpy(B).cuda().contiguous()
+    p = solve_params(m=20, tol=1e-10, precision=1, poly_degree=4, inner_tol=1e-5,
+                     flags=COARSE_ZERO_GUESS | COARSE_ODD_EVEN)
+    with pytest.raises(CoarseError) as e:
+        solve_batched([dev], [b], [torch.zeros_like(b)], p)
+    assert e.value.code == -1
+    dev.close()
