@@ -848,6 +848,9 @@ def run_batched(args):
                       "rhs_solves_per_s": round(nrhs / (ms / 1e3), 1), "operator_batches_per_s": round(1e3 / ms, 3),
                       "sequential_ms": round(ms_seq, 2), "speedup_vs_sequential": round(ms_seq / ms, 2),
                       "worst_rel_residual": worst, "kernel_launches_per_batch": infos[0]["kernel_launches"],
+                      "per_solve": {f: {"mean": round(statistics.mean(i[f] for i in infos), 2),
+                                        "max": max(i[f] for i in infos)}
+                                    for f in ("iterations", "cycles", "ir_steps", "recycle_updates")},
                       "generate_s": round(t_gen, 1), "setup_s": round(t_setup, 2), "clocks": clk.summary(),
                       "fp64_gmres_baseline": {"rhs_solves_per_s": round(rate64, 2), "right_hand_sides": n64,
                                               "operators": len(sample), "ms": round(ms64, 1),

@@ -490,7 +490,10 @@ extern "C" int coarse_solve_batched(coarse_op* const* ops, int nops, const void*
       for (int it = 0; k > 0 && sv->updates < p->recycle_updates && it < 3; ++it) {
         if ((rc = launch_fill_gaussian(tmp, N, p->seed * 7919ull + 31ull * i + it, s)) != COARSE_OK) break;
         coarse_solve_info inf;
-        int r2 = solve_column(op, sv, tmp, tmp + maxN, &ps, &inf, s, +1);
+        // the first setup solve builds the recycle space from a full GMRES(m) cycle (Sec. 3.4)
+        coarse_solve_params pi = ps;
+        if (sv->k_cur == 0) pi.flags |= COARSE_RECYCLE_FULL_CYCLE;
+        int r2 = solve_column(op, sv, tmp, tmp + maxN, &pi, &inf, s, +1);
         if (r2 != COARSE_OK && r2 != COARSE_ERR_NOT_CONVERGED) { rc = r2; break; }
         if (sv->k_cur == 0 && it >= 1) break;  // the solves converge before a recycle space forms
       }
