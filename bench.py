@@ -157,8 +157,13 @@ def build_operator(wl, device):
     return op, time.perf_counter() - t
 
 
+PIPELINED = {"on": False}
+
+
 def solver_params(cg, wl, k, extra=0, time_apply=False):
     flags = cg.COARSE_ZERO_GUESS | cg.COARSE_POLY_BF16 | cg.COARSE_ODD_EVEN | extra
+    if PIPELINED["on"]:
+        flags |= cg.COARSE_PIPELINED
     if time_apply:
         flags |= cg.COARSE_TIME_APPLY
     # FP32 inner solves to 2e-6: two refinement steps reach 1e-10 ((2e-6)^2 with margin)
@@ -417,13 +422,14 @@ def run_gb300(args):
                          "entries, every refinement step the FP64 blocks",
                    "polynomial_chain_blocks": "bf16",
                    "inner_system": "odd-even reduced, block-Jacobi preconditioned S = 1 - D_ee^-1 D_eo D_oo^-1 D_oe",
+                   "arnoldi": "latency-1 pipelined (Sec. 3.5)" if PIPELINED["on"] else "classical, CGS2",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(replicas.job_rate(args.steps, world, ms_e2e), 3), "unit": "solves/s",
                 "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
         "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
         "roofline": roofs[0] if roofs else None,
         "roofline_kernels": roofs,
-        "solver": {"iterations_per_solve": iters,
+        "solver": {"iterations_per_solve": iters, "breakdowns": sum(i["breakdowns"] for i in infos),
                    "matvecs_per_solve": statistics.mean(i["matvecs"] for i in infos),
                    "ir_steps": statistics.mean(i["ir_steps"] for i in infos),
                    "worst_rel_residual": max(i["rel_residual"] for i in infos),
@@ -863,6 +869,52 @@ def run_batched(args):
         o.close()
 
 
+def run_autograd(args):
+    """Differentiation workload: L = Re <c, D_c^{-1} b> on the Wilson-clover coarse 8^4, n = 32
+    operator (m0 = -0.42); one step = the forward solve and the backward pass (adjoint solve through
+    sigma3 D_c(-mu) sigma3 and the block gradients), FP32 inner solves with FP64 refinement."""
+    import torch
+
+    import paper_2205_09104_gb300 as cg
+    from synthetic import draws
+    dev = torch.device("cuda", 0)
+    wl = dict(WORKLOADS["wilson8"], key=(5, 0))
+    op, gen_s = build_operator(wl, dev)
+    n, V = op.n, op.volume
+    N = n * V
+    S = op.self_blocks.clone().requires_grad_()
+    H = op.hop_blocks.clone().requires_grad_()
+    cop = cg.CoarseOp(S.detach(), H.detach(), op.dims, op.nv, precisions=(cg.PREC_FP32, cg.PREC_BF16))
+    p = solver_params(cg, wl, wl["k"])
+    c, b, _ = draws.grad_draws((5, 1), N, V, n, 1)
+    bt = torch.from_numpy(b).to(dev).requires_grad_()
+    ct = torch.from_numpy(c).to(dev)
+
+    def step():
+        S.grad = H.grad = bt.grad = None
+        x = cg.CoarseSolve.apply(bt, S, H, cop, p)
+        loss = (ct.conj() * x).sum().real
+        loss.backward()
+        return loss
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"mode": "autograd", "workload": "wilson-clover coarse 8^4, nv=16 -> n=32, m0=-0.42; "
+                      "L = Re<c, D_c^-1 b>, forward + backward (adjoint solve + block gradients)",
+                      "steps_per_s": round(1e3 / ms, 2), "ms_per_step": round(ms, 3),
+                      "gradient_bytes_per_step": int((S.numel() + H.numel()) * 16),
+                      "clocks": clk.summary()}), flush=True)
+    cop.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -892,6 +944,10 @@ def main():
                     help="time the multi-right-hand-side tensor-core apply against the per-column path")
     ap.add_argument("--mrhs-case", default="",
                     help="one multi-right-hand-side case 'L,nv,nrhs' (coarse L^4, n = 2 nv)")
+    ap.add_argument("--pipelined", action="store_true",
+                    help="latency-1 pipelined Arnoldi (COARSE_PIPELINED) in the solves of the default line")
+    ap.add_argument("--autograd", action="store_true",
+                    help="time forward + backward of the differentiable solve (Wilson-clover 8^4, n = 32)")
     ap.add_argument("--batched", type=int, default=0,
                     help="time the lockstep batched engine on this many uneven operators")
     ap.add_argument("--batched-oddeven", default="on", choices=["on", "off"],
@@ -899,6 +955,10 @@ def main():
     ap.add_argument("--fp64-stride", type=int, default=4,
                     help="with --batched: plain FP64 GMRES on every n-th operator for the speedup")
     args = ap.parse_args()
+    PIPELINED["on"] = args.pipelined
+    if args.autograd:
+        run_autograd(args)
+        return
     if args.batched:
         run_batched(args)
         return

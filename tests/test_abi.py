@@ -51,3 +51,21 @@ def test_null_arguments_are_rejected_without_gpu(libpath):
     assert L.coarse_apply(None, None, None, 1, 0, None) == -1
     assert L.coarse_solve(None, None, None, 1, None, None, None) == -1
     assert L.coarse_solve_batched(None, -1, None, None, None, None, None, None) == -1
+
+
+def test_autotune_set_and_forget_without_gpu(libpath):
+    """coarse_autotune_set fixes a decision (plain key: every device) and a < 0 forgets it again;
+    both are host-side table operations, visible in coarse_autotune_report."""
+    L = ctypes.CDLL(libpath)
+    L.coarse_autotune_set.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.coarse_autotune_report.argtypes = [ctypes.c_char_p, ctypes.c_longlong]
+
+    def report():
+        buf = ctypes.create_string_buffer(1 << 14)
+        assert L.coarse_autotune_report(buf, len(buf)) == 0
+        return buf.value.decode()
+    assert L.coarse_autotune_set(b"eo/p1/n48/v16", 3, 0, 0) == 0
+    assert "eo/p1/n48/v16 -> 3 0 0" in report()
+    assert L.coarse_autotune_set(b"eo/p1/n48/v16", -1, 0, 0) == 0
+    assert "eo/p1/n48/v16 ->" not in report()
+    assert L.coarse_autotune_set(b"", 1, 0, 0) == -1
