@@ -194,8 +194,7 @@ def setup_solves(cg, cop, wl, k, S, X):
 # layouts of the odd-even half apply, by the autotuner's candidate number
 EO_LAYOUTS = {0: "k_eo_half[CTA of 4 warps]", 1: "k_eo_half_w[warp per site]", 2: "k_eo_half[CTA of 2 warps]",
               3: "k_eo_half[CTA of 2 warps, unrolled]", 4: "k_eo_half[CTA of 2 warps, prefetch]",
-              5: "k_eo_half[CTA of 2 warps, unrolled, prefetch]", 6: "k_eo_ring[streamed]",
-              7: "k_eo_half[CTA of 2 warps, unrolled, 12 CTAs per SM]"}
+              5: "k_eo_half[CTA of 2 warps, unrolled, prefetch]", 6: "k_eo_ring[streamed]"}
 
 
 def eo_layout(cg, prec, n):

@@ -357,10 +357,8 @@ __device__ __forceinline__ void eo_half_site(const EoArgs& a, const int k) {
   }
 }
 
-// MINB > 0 asks the compiler for MINB resident CTAs per SM (fewer registers per thread, more
-// loads in flight per SM); 0 keeps the default bound.
-template <int N, class BT, class VT, class AC, int W, bool UNROLL = false, bool PF = false, int MINB = 0>
-__global__ void __launch_bounds__(32 * W, MINB > 0 ? MINB : eo_min_blocks<N, AC, W, PF>()) k_eo_half(EoArgs a) {
+template <int N, class BT, class VT, class AC, int W, bool UNROLL = false, bool PF = false>
+__global__ void __launch_bounds__(32 * W, eo_min_blocks<N, AC, W, PF>()) k_eo_half(EoArgs a) {
   eo_half_site<N, BT, VT, AC, W, UNROLL, PF>(a, blockIdx.x);
 }
 
@@ -988,13 +986,6 @@ int launch_eo_ring_n(const EoArgs& a, cudaStream_t s) {
   return COARSE_OK;
 }
 
-// Layout 3 held to 12 resident CTAs per SM (4-byte accumulators only; FP64 would spill heavily).
-template <int N, class BT, class VT, class AC>
-void launch_eo_dense(int half, const EoArgs& a, cudaStream_t s) {
-  if constexpr (sizeof(decltype(AC{}.x)) == 4) k_eo_half<N, BT, VT, AC, 2, true, false, 12><<<half, 64, 0, s>>>(a);
-  else k_eo_half<N, BT, VT, AC, 2, true><<<half, 64, 0, s>>>(a);
-}
-
 template <class BT, class VT, class AC>
 int launch_eo_variant(int variant, int n, const EoArgs& a, cudaStream_t s) {
   const int half = a.V / 2;
@@ -1026,7 +1017,6 @@ int launch_eo_variant(int variant, int n, const EoArgs& a, cudaStream_t s) {
     else if (variant == 3) k_eo_half<NN, BT, VT, AC, 2, true><<<half, 64, 0, s>>>(a);            \
     else if (variant == 4) k_eo_half<NN, BT, VT, AC, 2, false, true><<<half, 64, 0, s>>>(a);     \
     else if (variant == 5) k_eo_half<NN, BT, VT, AC, 2, true, true><<<half, 64, 0, s>>>(a);      \
-    else if (variant == 7) launch_eo_dense<NN, BT, VT, AC>(half, a, s);                          \
     else k_eo_half<NN, BT, VT, AC, 4><<<half, 128, 0, s>>>(a);                                   \
     break;
   switch (n) {
@@ -1083,7 +1073,7 @@ int launch_eo_tuned(int prec, int n, const EoArgs& a, cudaStream_t s) {
     cudaStreamIsCapturing(s, &cap);
     TuneChoice c;
     std::vector<TuneChoice> cands;
-    for (int v = 0; v <= 7; ++v)
+    for (int v = 0; v <= 6; ++v)
       if (v < 6 || sizeof(decltype(AC{}.x)) == 4) cands.push_back(TuneChoice{v, 0, 0});
     const int rc = tune_pick(key, cands, run, s, &c);
     if (scratch) {
