@@ -745,6 +745,8 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
   while (rel > p->tol && inf.ir_steps < p->max_ir) {
     InnerInfo ii;
     const bool p1_step_now = s->pipelined && !s->p1_off;
+    // relative reduction the inner solve is asked for (the FP64 path solves to the final tolerance)
+    const double want = s->v64 ? 0.5 * p->tol * bn / rn : fmax(p->inner_tol, 0.5 * p->tol * bn / rn);
     if (p1_step_now)
       COARSE_CUDA(cudaMemcpyAsync(xkeep, x64, sizeof(double2) * (size_t)N, cudaMemcpyDeviceToDevice, stream));
     COARSE_CUDA(cudaMemsetAsync(s->e, 0, (s->v64 ? sizeof(double2) : sizeof(float2)) * (size_t)N, stream));
@@ -811,6 +813,13 @@ int solve_column(coarse_op* op, Solver* s, const double2* b64, double2* x64, con
       rn = rn_new;
       rel = rn / bn;
       continue;
+    }
+    if (p1_step_now && rn_new > sqrt(want) * rn) {
+      // a pipelined step that lowered the true residual by less than the square root of what its
+      // inner solve reported (the recurrence's residual estimate has drifted from the true one) is
+      // kept, and the solve goes on with classical cycles (counted as a breakdown)
+      s->p1_off = true;
+      inf.breakdowns++;
     }
     if (!isfinite(rn_new)) {
       set_error("non-finite residual during refinement");
