@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcoarse.so")
-SOURCES = ["api.cu", "apply.cu", "blas.cu", "dense.cu", "ops.cu", "solver.cu", "mrhs.cu", "batched.cu", "noalloc.cu", "tune.cu", "bmrhs.cu", "oddeven.cu", "measure.cu"]
+SOURCES = ["api.cu", "apply.cu", "blas.cu", "dense.cu", "ops.cu", "solver.cu", "mrhs.cu", "batched.cu", "noalloc.cu", "tune.cu", "bmrhs.cu", "oddeven.cu", "measure.cu", "mrhs_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

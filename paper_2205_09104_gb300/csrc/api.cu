@@ -77,6 +77,7 @@ void free_op(coarse_op* op) {
   if (op->eo_rec) cudaFree(op->eo_rec);
   if (op->eo_scratch) cudaFree(op->eo_scratch);
   if (op->mrhs_x.ptr) cudaFree(op->mrhs_x.ptr);
+  if (op->umma.ptr) cudaFree(op->umma.ptr);
   if (op->nb) cudaFree(op->nb);
   if (op->work64) cudaFree(op->work64);
   if (op->red) cudaFree(op->red);
@@ -333,8 +334,13 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
   if ((op->precisions & (1u << COARSE_PREC_BF16)) && op->max_nrhs > 1) {
     op->mrhs.bytes = nblk * sizeof(cbf16);
     CREATE_TRY(dmalloc((char**)&op->mrhs.ptr, op->mrhs.bytes));
-    op->mrhs_x.bytes = 12 * N * sizeof(cbf16);
+    // 12 columns as mma.sync fragments, or as the two tcgen05 B-operand variants (twice that)
+    op->mrhs_x.bytes = 24 * N * sizeof(cbf16);
     CREATE_TRY(dmalloc((char**)&op->mrhs_x.ptr, op->mrhs_x.bytes));
+    if (op->n == 32 || op->n == 48) {
+      op->umma.bytes = nblk * sizeof(cbf16);
+      CREATE_TRY(dmalloc((char**)&op->umma.ptr, op->umma.bytes));
+    }
   }
   CREATE_TRY(dmalloc(&op->work64, 3 * N * sizeof(double2)));
   CREATE_TRY(dmalloc((char**)&op->apply_scratch, 5 * N * sizeof(double2)));

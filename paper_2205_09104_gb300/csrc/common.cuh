@@ -81,7 +81,8 @@ struct coarse_op {
   int* nb = nullptr;                // device int32 [V][8]
   coarse::Blocks blk[3];            // FP64, FP32, BF16 copies
   coarse::Blocks mrhs;              // BF16 blocks in the tensor-core fragment layout (BF16 and max_nrhs > 1)
-  coarse::Blocks mrhs_x;            // 12 columns of BF16 vector fragments (scratch of the multi-RHS apply)
+  coarse::Blocks mrhs_x;            // packed BF16 columns of one multi-RHS pass (scratch of the multi-RHS apply)
+  coarse::Blocks umma;              // BF16 blocks as tcgen05 core-matrix planes (n = 32, 48; BF16 and max_nrhs > 1)
   // odd-even reduction (all extents even): site lists and inverses of the diagonal blocks
   int* eo_sites = nullptr;          // device [V]: even sites, then odd sites, each in increasing order
   int* eo_half = nullptr;           // device [V]: position of each site in its parity's list

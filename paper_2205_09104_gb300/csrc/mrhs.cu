@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "mrhs_ring.cuh"
+#include "mrhs_tc.cuh"
 #include "tune.cuh"
 
 namespace coarse {
@@ -72,6 +73,7 @@ struct MrhsArgs {
   float mu;           // signed twisted mass (-mu for the adjoint)
   int adj;
   int* err;
+  const void* tcblk;  // the blocks as tcgen05 core-matrix planes (null: the tcgen05 kernel is not offered)
 };
 
 template <int N, int P> struct MrhsShape {
@@ -159,8 +161,9 @@ int launch_mrhs_cfg(MrhsArgs a, int S, cudaStream_t s) {
 }
 
 // configurations offered to the autotuner: (P, S); the first is the static default
-template <int N>
-std::vector<TuneChoice> mrhs_candidates() {
+// (P = 100 + c: the tcgen05 kernel with c CTAs per SM, stages S (0: all that fit), issue order c)
+template <int N, int T>
+std::vector<TuneChoice> mrhs_candidates(bool tc) {
   std::vector<TuneChoice> c;
   const int def_p = N == 16 ? 4 : (N == 32 ? 2 : 1);
   const int ps[3] = {N == 16 ? 2 : 1, N == 16 ? 4 : 2, N == 16 ? 8 : 4};
@@ -170,17 +173,57 @@ std::vector<TuneChoice> mrhs_candidates() {
     for (int S : {3, 5, 8})
       if (!(P == def_p && S == 0)) c.push_back({P, S, 0});
   }
+  if (tc && (N == 32 || N == 48)) {  // c: the tcgen05 kernel's issue order
+    const int max_ctas = T <= 2 ? 4 : 2;  // tensor-memory columns: 128 per CTA for T <= 2, else 256
+    for (int il : {1, 0})
+      for (int k = 1; k <= max_ctas; ++k) c.push_back({100 + k, 0, il});
+  }
   return c;
+}
+
+// the columns as mma.sync B fragments (k_pack_mrhs_x), then the mma.sync kernel
+template <int N, int T, int P>
+int launch_mrhs_frag(const MrhsArgs& a, int S, cudaStream_t s) {
+  const size_t total = (size_t)a.V * (kMrhsTile * T) * (N / 2);
+  size_t grid = (total + 255) / 256;
+  if (grid > (size_t)sm_count() * 16) grid = (size_t)sm_count() * 16;
+  k_pack_mrhs_x<<<(int)grid, 256, 0, s>>>(a.x, a.ldx, a.R, T, a.V, N, (uint32_t*)a.xb);
+  note_launch();
+  COARSE_CUDA(cudaGetLastError());
+  return launch_mrhs_cfg<N, T, P>(a, S, s);
 }
 
 template <int N, int T>
 int launch_mrhs_choice(const MrhsArgs& a, const TuneChoice& c, cudaStream_t s) {
   switch (c.a) {
-    case 1: return launch_mrhs_cfg<N, T, 1>(a, c.b, s);
-    case 2: return launch_mrhs_cfg<N, T, 2>(a, c.b, s);
-    case 4: return launch_mrhs_cfg<N, T, 4>(a, c.b, s);
+    case 1: return launch_mrhs_frag<N, T, 1>(a, c.b, s);
+    case 2: return launch_mrhs_frag<N, T, 2>(a, c.b, s);
+    case 4: return launch_mrhs_frag<N, T, 4>(a, c.b, s);
     case 8:
-      if constexpr (N == 16) return launch_mrhs_cfg<N, T, 8>(a, c.b, s);
+      if constexpr (N == 16) return launch_mrhs_frag<N, T, 8>(a, c.b, s);
+      break;
+    case 101:
+    case 102:
+    case 103:
+    case 104:
+      if (a.tcblk) {
+        TcArgs t{};
+        t.blk = static_cast<const unsigned char*>(a.tcblk);
+        t.nb = a.nb;
+        t.x = a.x;
+        t.xv = (unsigned char*)const_cast<uint2*>(a.xb);
+        t.y = a.y;
+        t.ldx = a.ldx;
+        t.ldy = a.ldy;
+        t.R = a.R;
+        t.V = a.V;
+        t.n = N;
+        t.mu = a.mu;
+        t.adj = a.adj;
+        t.il = c.c;
+        t.err = a.err;
+        return launch_apply_mrhs_tc(t, T, c.a - 100, c.b, s);
+      }
       break;
   }
   set_error("multi-RHS apply: no configuration with %d sites per stage for n = %d", c.a, N);
@@ -192,7 +235,7 @@ int launch_mrhs_t(const MrhsArgs& a, cudaStream_t s) {
   char key[96];
   snprintf(key, sizeof(key), "mrhs/n%d/t%d/v%d", N, T, tune_bucket(a.V));
   TuneChoice c;
-  int rc = tune_pick(key, mrhs_candidates<N>(), [&](const TuneChoice& ch) { return launch_mrhs_choice<N, T>(a, ch, s); },
+  int rc = tune_pick(key, mrhs_candidates<N, T>(a.tcblk != nullptr), [&](const TuneChoice& ch) { return launch_mrhs_choice<N, T>(a, ch, s); },
                      s, &c);
   if (rc != COARSE_OK) return rc;
   return launch_mrhs_choice<N, T>(a, c, s);
@@ -213,6 +256,10 @@ int launch_mrhs_n(const MrhsArgs& a, cudaStream_t s) {
 
 int launch_pack_mrhs(const coarse_op* op, cudaStream_t s) {
   if (!op->mrhs.ptr) return COARSE_OK;
+  if (op->umma.ptr) {
+    const int rc = launch_pack_tc(op->blk[COARSE_PREC_BF16].ptr, op->umma.ptr, (long long)op->V * 5, op->n, s);
+    if (rc != COARSE_OK) return rc;
+  }
   const size_t total = (size_t)op->V * 5 * op->n * op->n;
   size_t grid = (total + 255) / 256;
   if (grid > (size_t)sm_count() * 16) grid = (size_t)sm_count() * 16;
@@ -242,15 +289,7 @@ int launch_apply_mrhs_bf16(const coarse_op* op, const void* x, void* y, int nrhs
     a.y = (float2*)y + c0 * col;
     a.ldx = a.ldy = col;
     a.R = nrhs - c0 < kMrhsPass ? nrhs - c0 : kMrhsPass;
-    {
-      const int T = (a.R + kMrhsTile - 1) / kMrhsTile;
-      const size_t total = (size_t)op->V * (kMrhsTile * T) * (op->n / 2);
-      size_t grid = (total + 255) / 256;
-      if (grid > (size_t)sm_count() * 16) grid = (size_t)sm_count() * 16;
-      k_pack_mrhs_x<<<(int)grid, 256, 0, s>>>(a.x, a.ldx, a.R, T, op->V, op->n, (uint32_t*)op->mrhs_x.ptr);
-      note_launch();
-      COARSE_CUDA(cudaGetLastError());
-    }
+    a.tcblk = op->umma.ptr;
     a.V = op->V;
     a.mu = (float)(adjoint ? -op->mu : op->mu);
     a.adj = adjoint;
