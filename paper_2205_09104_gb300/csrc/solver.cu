@@ -555,8 +555,12 @@ int Solver::inner(double target_abs, int max_cycles, int m, int kdef, int ulimit
     // r -= V_{j+1} (Hbar y_V)
     TRY(launch_update(v64, (const void* const*)vtab, j + 1, dn.z, 1, r, N, 1, nullptr, norm2, partial, counter, nostop,
                       stream));
-    // recycle space (Sec. 3.4): first extraction needs more than k steps; then up to ulimit updates
-    const bool can = kdef > 0 && updates < ulimit && ((kc == 0 && j > kdef) || (kc > 0 && j >= 1));
+    // recycle space (Sec. 3.4): first extraction needs more than k steps; then up to ulimit updates.
+    // A pipelined cycle in FP32 / BF16 makes no update: its Hessenberg entries come from
+    // t = ||v^a||^2 - sum |h|^2 (Sec. 3.5), whose cancellation leaves them too inexact for the
+    // harmonic Ritz update (A U = C degraded to 4e-3 on the twisted-mass lattice); FP64 ones do.
+    const bool can = kdef > 0 && updates < ulimit && !(p1_active && !v64) &&
+                     ((kc == 0 && j > kdef) || (kc > 0 && j >= 1));
     if (can) {
       for (int c = 0; c < kc; ++c)
         TRY(launch_multidot(v64, (const void* const*)qtab[par], kc + j + 1, U[par][c], N, SW + (size_t)c * ldsw,
