@@ -67,23 +67,23 @@ def peaks():
 
 
 def profiled_traffic(workload):
-    """DRAM bytes per S apply by block precision from the ncu summary of the odd-even half apply on
-    this workload (profiles/k_eo_half_<workload>.md, line 'traffic_per_S_apply: fp32=<B> bf16=<B>'),
-    or {} when no summary is committed."""
+    """DRAM bytes per S apply by half-apply layout and block precision, from the ncu summary of
+    the odd-even half apply on this workload (profiles/k_eo_half_<workload>.md, lines
+    'traffic_per_S_apply layout=<v>: fp32=<B> bf16=<B>'): {(layout, "fp32"|"bf16"): bytes}, or {}
+    when no summary is committed."""
     path = os.path.join(PROFILES, f"k_eo_half_{workload}.md")
+    out = {}
     try:
         with open(path) as f:
             for line in f:
-                m = re.match(r"\s*traffic_per_S_apply:\s*(.*)", line)
+                m = re.match(r"\s*traffic_per_S_apply\s+layout=(\d+):\s*(.*)", line)
                 if m:
-                    out = {}
-                    for kv in m.group(1).split():
+                    for kv in m.group(2).split():
                         k, v = kv.split("=")
-                        out[k] = float(v)
-                    return out, os.path.relpath(path, ROOT)
+                        out[(int(m.group(1)), k)] = float(v)
     except OSError:
         pass
-    return {}, None
+    return out, (os.path.relpath(path, ROOT) if out else None)
 
 
 class ClockSampler:
@@ -197,12 +197,17 @@ EO_LAYOUTS = {0: "k_eo_half[CTA of 4 warps]", 1: "k_eo_half_w[warp per site]", 2
               5: "k_eo_half[CTA of 2 warps, unrolled, prefetch]", 6: "k_eo_ring[streamed]"}
 
 
-def eo_layout(cg, prec, n):
-    """Name of the half-apply layout the autotuner chose for block precision `prec`."""
+def eo_choice(cg, prec, n):
+    """Half-apply layout number the autotuner chose for block precision `prec`, or None."""
     for line in cg.autotune_report().splitlines():
         if line.startswith(f"eo/p{prec}/n{n}/") and "->" in line:
-            return EO_LAYOUTS.get(int(line.split("->")[1].split()[0]), "k_eo_half")
-    return "k_eo_half"
+            return int(line.split("->")[1].split()[0])
+    return None
+
+
+def eo_layout(cg, prec, n):
+    """Name of the half-apply layout the autotuner chose for block precision `prec`."""
+    return EO_LAYOUTS.get(eo_choice(cg, prec, n), "k_eo_half")
 
 
 def roofline_entries(cg, tinfos, n, peak, src, workload):
@@ -219,8 +224,8 @@ def roofline_entries(cg, tinfos, n, peak, src, workload):
         achieved = by / (ms * 1e-3) / 1e9
         bt = "float2" if q == cg.PREC_FP32 else "cbf16"
         out.append({"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "traffic": traffic.get(name),
-                    "traffic_source": tsrc if name in traffic else None,
+                    "frac": round(achieved / peak, 4), "traffic": traffic.get((eo_choice(cg, q, n), name)),
+                    "traffic_source": tsrc if (eo_choice(cg, q, n), name) in traffic else None,
                     "kernel": f"{eo_layout(cg, q, n)}<{n},{bt}> x2 ({role}); one launch = one S apply = two "
                               "half passes",
                     "bytes_per_launch": round(by / cnt), "avg_launch_us": round(ms / cnt * 1e3, 2),
