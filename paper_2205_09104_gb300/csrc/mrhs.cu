@@ -161,7 +161,7 @@ int launch_mrhs_cfg(MrhsArgs a, int S, cudaStream_t s) {
 }
 
 // configurations offered to the autotuner: (P, S); the first is the static default
-// (P = 100 + c: the tcgen05 kernel with c CTAs per SM, stages S (0: all that fit), issue order c)
+// (P = 100 + k: the tcgen05 kernel with k CTAs per SM and stages S, 0: all that fit)
 template <int N, int T>
 std::vector<TuneChoice> mrhs_candidates(bool tc) {
   std::vector<TuneChoice> c;
@@ -173,10 +173,9 @@ std::vector<TuneChoice> mrhs_candidates(bool tc) {
     for (int S : {3, 5, 8})
       if (!(P == def_p && S == 0)) c.push_back({P, S, 0});
   }
-  if (tc && (N == 32 || N == 48)) {  // c: the tcgen05 kernel's issue order
-    const int max_ctas = T <= 2 ? 4 : 2;  // tensor-memory columns: 128 per CTA for T <= 2, else 256
-    for (int il : {1, 0})
-      for (int k = 1; k <= max_ctas; ++k) c.push_back({100 + k, 0, il});
+  if (tc && (N == 32 || N == 48)) {
+    const int max_ctas = T <= 2 ? 3 : 2;  // tensor-memory columns: 128 per CTA for T <= 2, else 256
+    for (int k = 1; k <= max_ctas; ++k) c.push_back({100 + k, 0, 0});
   }
   return c;
 }
@@ -205,7 +204,6 @@ int launch_mrhs_choice(const MrhsArgs& a, const TuneChoice& c, cudaStream_t s) {
     case 101:
     case 102:
     case 103:
-    case 104:
       if (a.tcblk) {
         TcArgs t{};
         t.blk = static_cast<const unsigned char*>(a.tcblk);
@@ -220,7 +218,6 @@ int launch_mrhs_choice(const MrhsArgs& a, const TuneChoice& c, cudaStream_t s) {
         t.n = N;
         t.mu = a.mu;
         t.adj = a.adj;
-        t.il = c.c;
         t.err = a.err;
         return launch_apply_mrhs_tc(t, T, c.a - 100, c.b, s);
       }

@@ -33,18 +33,21 @@
 // Accumulators of an M = 64 product occupy tensor-memory lanes 0..15 of each 32-lane quarter
 // (row 16 e + l in lane 32 e + l), also checked on the device.
 //
-// Pipeline (one CTA of 6 warps, persistent over sites x = blockIdx.x + k gridDim.x): warp 0
-// lane 0 brings each of a site's 9 items (block + column variant, two bulk copies) into a ring
-// of S shared-memory stages ("full" mbarriers); warp 1 lane 0 issues the item's 2 x n/16 MMAs
-// into one of two accumulator sets in tensor memory and releases the stage through
-// tcgen05.commit ("empty"); after the 9th item it commits the set to the epilogue ("acc full").
-// MMAs into one accumulator complete in order, one after the other; with issue order il = 1
-// the items come as self, then (forward mu, backward mu) pairs, and the MMAs of a pair are
-// issued K step by K step over both planes and both items, so that consecutive MMAs go to four
-// different accumulators (forward / backward x real / imaginary plane).
-// Warps 2..5 (one per tensor-memory lane quarter) read the set, free it ("acc empty") and
-// combine and store the site's output rows.  Every wait is bounded: on expiry the kernel raises
-// *err, drains its bulk copies and MMAs (bounded again), frees its tensor memory and returns.
+// Pipeline (one CTA of 9 warps, persistent over sites x = blockIdx.x + k gridDim.x): warp 0
+// lane 0 brings each of a site's 9 items (block + column variant, two bulk copies) into one of
+// two rings of shared-memory stages ("full" mbarriers): self and forward hops into one,
+// backward hops into the other, so that every stage's consumers take each of its phases in
+// turn (a parity wait never sees a phase two ahead).  Warps 1..4 issue the MMAs, one lane each, and
+// each owns one of a site's four accumulators (forward / backward hops x real / imaginary
+// plane): a thread's tcgen05.mma stream advances by one instruction about every 160 cycles
+// whatever M, N or the dependences between them (measured), so the MMAs of a site are spread
+// over four issuing threads.  Each issuer releases a stage through tcgen05.commit ("empty",
+// two arrivals: both planes of the item) and, after its last item of the site, commits the
+// accumulator set to the epilogue ("acc full", four arrivals).  Warps 5..8 (one per
+// tensor-memory lane quarter) read the set in chunks of four columns, combine and store the
+// site's output rows, and free the set ("acc empty").  Every wait is bounded: on expiry the
+// kernel raises *err, drains its bulk copies and MMAs (bounded again), frees its tensor memory
+// and returns.
 #include <cstdint>
 #include <cstdio>
 
@@ -54,11 +57,16 @@
 namespace coarse {
 namespace {
 
-constexpr int kTcThreads = 192;
+constexpr int kTcThreads = 288;
 constexpr uint32_t kTcPad = 2048;      // shared memory after the ring (over-read of M = 64 operands)
 
+// Stages of the self / forward ring out of S in all (the rest hold backward hops), >= 2 each.
+__host__ __device__ constexpr int tc_split(int S) {
+  return (5 * S + 4) / 9 < 2 ? 2 : ((5 * S + 4) / 9 > S - 2 ? S - 2 : (5 * S + 4) / 9);
+}
+
 // Tensor-memory columns: 2 accumulator sets x 4 accumulators of width N = 8T, in slots of 16
-// columns (T <= 2: 128 columns per CTA, up to 4 CTAs per SM) or 32 (T = 3: 256, up to 2).
+// columns (T <= 2: 128 columns per CTA, up to 3 CTAs per SM) or 32 (T = 3: 256, up to 2).
 __host__ __device__ constexpr uint32_t tc_slot(int T) { return T <= 2 ? 16u : 32u; }
 __host__ __device__ constexpr uint32_t tc_cols(int T) { return 8u * tc_slot(T); }
 
@@ -88,13 +96,13 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+__device__ __forceinline__ void tc_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // BF16 blocks [V][5][n][n] (complex, re in the low half) -> the core-matrix planes above.  One
@@ -147,27 +155,21 @@ __global__ void k_pack_tc_x(const float2* __restrict__ x, long long ldx, int R, 
   }
 }
 
-// item order of a site: b = 0 self, 1..4 forward mu = b - 1, 5..8 backward mu = b - 5
-__device__ __forceinline__ int tc_item(int il, int i) {
-  // il = 1: self, then the forward and backward hop of each direction next to each other
-  return il ? (i == 0 ? 0 : ((i & 1) ? (i + 1) / 2 : 4 + i / 2)) : i;
-}
-
 template <int N, int T>
-__global__ void __launch_bounds__(kTcThreads, 1) k_apply_mrhs_tc(const __grid_constant__ TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_apply_mrhs_tc(const __grid_constant__ TcArgs a) {
   constexpr int G = N / 8, KS = N / 16, NN = 8 * T;
   constexpr uint32_t PLANE = (uint32_t)N * N * 2, BLK = 2 * PLANE, VB = (uint32_t)NN * N * 2, SB = BLK + VB;
   constexpr uint32_t SBO = (uint32_t)G * 128;
   constexpr uint32_t ID_K = tc_idesc(64, NN, 0), ID_MN = tc_idesc(64, NN, 1);
   constexpr uint32_t SLOT = tc_slot(T), COLS = tc_cols(T);
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int S = a.S;
+  const int S = a.S, Sf = tc_split(S), Sb = S - Sf;  // stages [0, Sf): forward ring, [Sf, S): backward
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB + kTcPad);
   uint64_t* empty = full + S;
   uint64_t* accf = empty + S;   // [2]
   uint64_t* acce = accf + 2;    // [2]
-  uint64_t* done = acce + 2;    // the MMA issuer's final commit
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* done = acce + 2;    // [4]: each MMA issuer's final commit
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int my_sites = (int)blockIdx.x < a.V ? (a.V - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int items = my_sites * 9;
@@ -175,13 +177,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_mrhs_tc(const __grid_co
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(full + i, 1);
-      mbar_init(empty + i, 1);
+      mbar_init(empty + i, 2);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(accf + i, 1);
+      mbar_init(accf + i, 4);
       mbar_init(acce + i, 4);
     }
-    mbar_init(done, 1);
+    for (int i = 0; i < 4; ++i) mbar_init(done + i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_mrhs_tc(const __grid_co
 
   if (warp == 0) {  // ------------------------------------------------------------ producer
     if (lane == 0) {
-      int ok = 1, it = 0;
+      int ok = 1, it = 0, jf = 0, jb = 0;  // items issued per ring
       // neighbour rows of the current and (prefetched) next site
       int4 lo = make_int4(0, 0, 0, 0), hi = lo, nlo = lo, nhi = lo;
       if (my_sites > 0) {
@@ -204,8 +206,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_mrhs_tc(const __grid_co
         nhi = __ldg(reinterpret_cast<const int4*>(a.nb + (size_t)blockIdx.x * 8 + 4));
       }
       for (; it < items; ++it) {
-        const int slot = it % S, b = tc_item(a.il, it % 9), sk = it / 9;
+        const int b = it % 9, sk = it / 9;
         const int x = (int)blockIdx.x + sk * (int)gridDim.x;
+        const int bw = b >= 5, Sx = bw ? Sb : Sf, j = bw ? jb : jf;
+        const int slot = (bw ? Sf : 0) + j % Sx;
         if (it % 9 == 0) {
           lo = nlo;
           hi = nhi;
@@ -215,10 +219,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_mrhs_tc(const __grid_co
             nhi = __ldg(reinterpret_cast<const int4*>(a.nb + (size_t)xn * 8 + 4));
           }
         }
-        if (it >= S && !mbar_wait_suspend(empty + slot, (uint32_t)((it / S - 1) & 1))) {
+        if (j >= Sx && !mbar_wait_suspend(empty + slot, (uint32_t)((j / Sx - 1) & 1))) {
           ok = 0;
           break;
         }
+        if (bw) ++jb;
+        else ++jf;
         int src = x;
         switch (b) {
           case 1: src = lo.x; break;
@@ -239,54 +245,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_mrhs_tc(const __grid_co
       }
       if (!ok) {
         atomicExch(a.err, 1);
-        for (int j = it - S < 0 ? 0 : it - S; j < it; ++j) mbar_wait(full + (j % S), (uint32_t)((j / S) & 1));
+        // drain the copies still in flight in either ring (bounded)
+        for (int k = jf - Sf < 0 ? 0 : jf - Sf; k < jf; ++k) mbar_wait(full + k % Sf, (uint32_t)((k / Sf) & 1));
+        for (int k = jb - Sb < 0 ? 0 : jb - Sb; k < jb; ++k) mbar_wait(full + Sf + k % Sb, (uint32_t)((k / Sb) & 1));
       }
     }
-  } else if (warp == 1) {  // ---------------------------------------------------- MMA issuer
+  } else if (warp <= 4) {  // --------------------------------------------------- MMA issuers
     if (lane == 0) {
+      // issuer (bwd, p): items of one hop direction type (self + forward: 0..4, backward: 5..8),
+      // plane p, into its own accumulator
+      const int bwd = (warp - 1) >> 1, p = (warp - 1) & 1;
+      const int b0 = bwd ? 5 : 0, b1 = bwd ? 9 : 5;
       int ok = 1;
       const uint32_t s0 = smem_u32(smem);
-      // groups of items issued together: il = 0 one item at a time; il = 1 the self item, then
-      // pairs (forward mu, backward mu)
-      const int ngroups = a.il ? 5 : 9;
       for (int sk = 0; sk < my_sites && ok; ++sk) {
         const int buf = sk & 1;
         if (sk >= 2) {
           if (!mbar_wait_suspend(acce + buf, (uint32_t)((sk / 2 - 1) & 1))) { ok = 0; break; }
           tc_fence_after();
         }
-        for (int g = 0; g < ngroups && ok; ++g) {
-          const int i0 = a.il ? (g == 0 ? 0 : 2 * g - 1) : g, cnt = (a.il && g > 0) ? 2 : 1;
-          uint32_t st[2];
-          int bb[2];
-          for (int c = 0; c < cnt; ++c) {
-            const int it = sk * 9 + i0 + c;
-            if (!mbar_wait_suspend(full + it % S, (uint32_t)((it / S) & 1))) { ok = 0; break; }
-            st[c] = s0 + (uint32_t)(it % S) * SB;
-            bb[c] = tc_item(a.il, i0 + c);
-          }
-          if (!ok) break;
+        const uint32_t d = tmem + (uint32_t)buf * 4u * SLOT + (uint32_t)(bwd * 2 + p) * SLOT;
+        const int Sx = bwd ? Sb : Sf, cnt = b1 - b0;
+        for (int b = b0; b < b1; ++b) {
+          const int j = sk * cnt + (b - b0), slot = (bwd ? Sf : 0) + j % Sx;
+          if (!mbar_wait_suspend(full + slot, (uint32_t)((j / Sx) & 1))) { ok = 0; break; }
           tc_fence_after();
+          const uint32_t st = s0 + (uint32_t)slot * SB;
 #pragma unroll
-          for (int s = 0; s < KS; ++s)
-            for (int c = 0; c < cnt; ++c) {
-              const int b = bb[c], bwd = b >= 5;
-#pragma unroll
-              for (int p = 0; p < 2; ++p) {
-                const uint64_t ad = bwd ? tc_sdesc(st[c] + p * PLANE + 2u * s * SBO, SBO, 128u)  // F^T: K stride G*128
-                                        : tc_sdesc(st[c] + p * PLANE + 256u * s, 128u, SBO);     // F: K stride 128
-                const uint64_t bd = tc_sdesc(st[c] + BLK + 256u * s, 128u, SBO);
-                const uint32_t d = tmem + (uint32_t)buf * 4u * SLOT + (uint32_t)(bwd * 2 + p) * SLOT;
-                tc_mma(d, ad, bd, bwd ? ID_MN : ID_K, (s > 0 || (b != 0 && b != 5)) ? 1u : 0u);
-              }
-            }
-          for (int c = 0; c < cnt; ++c) tc_commit(empty + (sk * 9 + i0 + c) % S);
+          for (int s = 0; s < KS; ++s) {
+            const uint64_t ad = bwd ? tc_sdesc(st + p * PLANE + 2u * s * SBO, SBO, 128u)    // F^T: K stride G*128
+                                    : tc_sdesc(st + p * PLANE + 256u * s, 128u, SBO);       // F: K stride 128
+            const uint64_t bd = tc_sdesc(st + BLK + 256u * s, 128u, SBO);
+            tc_mma(d, ad, bd, bwd ? ID_MN : ID_K, (s > 0 || b != b0) ? 1u : 0u);
+          }
+          tc_commit(empty + slot);
         }
         if (ok) tc_commit(accf + buf);
       }
       if (!ok) atomicExch(a.err, 1);
-      tc_commit(done);  // completes when every MMA issued above has completed
-      mbar_wait(done, 0);
+      tc_commit(done + (warp - 1));  // completes when every MMA this thread issued has completed
+      mbar_wait(done + (warp - 1), 0);
     }
   } else {  // ------------------------------------------------------------------- epilogue
     const int e = warp & 3;                   // tensor-memory lane quarter of this warp
@@ -299,45 +297,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_mrhs_tc(const __grid_co
       if (!mbar_wait_suspend(accf + buf, (uint32_t)((sk / 2) & 1))) ok = 0;
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      float P[2][NN], Q[2][NN];
       const uint32_t base = tmem + ((uint32_t)(32 * e) << 16) + (uint32_t)buf * 4u * SLOT;
+      const int x = (int)blockIdx.x + sk * (int)gridDim.x;
+      constexpr int C = 4 * T;
+      // four columns at a time: for column q the real parts sit in accumulator column q, the
+      // imaginary parts in column C + q, of each of the four accumulators
 #pragma unroll
-      for (int p = 0; p < 2; ++p)
+      for (int q0 = 0; q0 < C; q0 += 4) {
+        float pr[2][4], pi[2][4], qr[2][4], qi[2][4];
 #pragma unroll
-        for (int c = 0; c < T; ++c) {
-          float v[8];
-          tc_ld8(base + (uint32_t)p * SLOT + 8u * c, v);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) P[p][8 * c + i] = v[i];
-          tc_ld8(base + (uint32_t)(2 + p) * SLOT + 8u * c, v);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) Q[p][8 * c + i] = v[i];
+        for (int pl = 0; pl < 2; ++pl) {
+          tc_ld4(base + (uint32_t)pl * SLOT + (uint32_t)q0, pr[pl]);
+          tc_ld4(base + (uint32_t)pl * SLOT + (uint32_t)(C + q0), pi[pl]);
+          tc_ld4(base + (uint32_t)(2 + pl) * SLOT + (uint32_t)q0, qr[pl]);
+          tc_ld4(base + (uint32_t)(2 + pl) * SLOT + (uint32_t)(C + q0), qi[pl]);
         }
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (r >= 0 && r < N) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int q = q0 + j;
+            if (q >= a.R) break;
+            // forward F w and backward F^H w' of column q, then y = o (fwd + s bwd + i mu' v)
+            float yr = pr[0][j] - pi[1][j] + s * (qr[0][j] + qi[1][j]);
+            float yi = pi[0][j] + pr[1][j] + s * (qi[0][j] - qr[1][j]);
+            if (a.mu != 0.f) {
+              const float2 v = __ldg(a.x + q * a.ldx + (size_t)x * N + r);
+              yr -= m * v.y;
+              yi += m * v.x;
+            }
+            if (a.adj) {
+              yr *= s;
+              yi *= s;
+            }
+            a.y[q * a.ldy + (size_t)x * N + r] = make_float2(yr, yi);
+          }
+        }
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acce + buf);
-      if (r >= 0 && r < N) {
-        const int x = (int)blockIdx.x + sk * (int)gridDim.x;
-        constexpr int C = 4 * T;
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-          if (q >= a.R) break;
-          // forward F w and backward F^H w' of column q, then y = o (fwd + s bwd + i mu' v)
-          float yr = P[0][q] - P[1][C + q] + s * (Q[0][q] + Q[1][C + q]);
-          float yi = P[0][C + q] + P[1][q] + s * (Q[0][C + q] - Q[1][q]);
-          if (a.mu != 0.f) {
-            const float2 v = __ldg(a.x + q * a.ldx + (size_t)x * N + r);
-            yr -= m * v.y;
-            yi += m * v.x;
-          }
-          if (a.adj) {
-            yr *= s;
-            yi *= s;
-          }
-          a.y[q * a.ldy + (size_t)x * N + r] = make_float2(yr, yi);
-        }
-      }
     }
     if (!ok && lane == 0) atomicExch(a.err, 1);
   }
@@ -354,17 +353,18 @@ int launch_tc_nt(TcArgs a, int ctas_per_sm, int S, cudaStream_t s) {
   constexpr uint32_t SB = 4u * N * N + 16u * T * N;
   // ctas_per_sm CTAs share the SM's shared memory; the shared memory of each is also at least
   // what keeps one more CTA (and one more tensor-memory allocation) off the SM
-  if (ctas_per_sm < 1 || ctas_per_sm > 4 || ctas_per_sm * tc_cols(T) > 512u) {
+  // registers (9 warps of up to 72) allow 3 CTAs per SM; tensor memory 512 columns
+  if (ctas_per_sm < 1 || ctas_per_sm > 3 || ctas_per_sm * tc_cols(T) > 512u) {
     set_error("tcgen05 multi-RHS apply: %d CTAs per SM with %u tensor-memory columns each", ctas_per_sm, tc_cols(T));
     return COARSE_ERR_INVALID_ARG;
   }
   const size_t sm_bytes = 228u * 1024u, reserve = 1024u;
   const size_t budget = sm_bytes / ctas_per_sm - reserve > 210u * 1024u ? 210u * 1024u : sm_bytes / ctas_per_sm - reserve;
   const size_t floor_bytes = sm_bytes / (ctas_per_sm + 1) + 1024u;
-  const size_t fixed = kTcPad + (2 * 32 + 5) * sizeof(uint64_t) + 16;
+  const size_t fixed = kTcPad + (2 * 32 + 8) * sizeof(uint64_t) + 16;
   if (S <= 0) S = (int)((budget - fixed) / SB);
-  S = S < 2 ? 2 : (S > 32 ? 32 : S);
-  while (S > 2 && S * SB + fixed > budget) --S;
+  S = S < 4 ? 4 : (S > 32 ? 32 : S);  // two rings of at least 2 stages
+  while (S > 4 && S * SB + fixed > budget) --S;
   a.S = S;
   size_t smem = (size_t)S * SB + fixed;
   if (smem < floor_bytes) smem = floor_bytes;

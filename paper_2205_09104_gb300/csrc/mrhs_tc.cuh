@@ -19,15 +19,13 @@ struct TcArgs {
   int S;                     // pipeline stages (set by the launcher)
   float mu;                  // signed twisted mass (-mu for the adjoint)
   int adj;
-  int il;                    // issue order: 0 = item by item, 1 = forward and backward hop of a
-                             // direction interleaved (four independent accumulators in flight)
   int* err;
 };
 
 // Refresh the core-matrix planes from the BF16 blocks ([nblocks][n][n] complex BF16).
 int launch_pack_tc(const void* bf16_blocks, void* dst, long long nblocks, int n, cudaStream_t s);
 // Pack the R columns of a.x and apply (n = 32 or 48, T = 1 .. 3 column tiles of 4), with
-// ctas_per_sm = 1 or 2 CTAs per SM, S stages (S <= 0: as many as fit) and issue order a.il.
+// ctas_per_sm = 1 .. 3 CTAs per SM (3 only for T <= 2) and S stages (S <= 0: as many as fit).
 int launch_apply_mrhs_tc(TcArgs a, int T, int ctas_per_sm, int S, cudaStream_t s);
 
 }  // namespace coarse
