@@ -22,8 +22,12 @@ __device__ __forceinline__ void store_vec(VT* p, const AC (&w)[CPL]) {
   for (int c = 0; c < CPL; ++c) { VT v; v.x = w[c].x; v.y = w[c].y; p[c] = v; }
 }
 
-// Streaming (read-once) block loads: evict-first so that the per-site pushes stay in L2.
-template <class T> __device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
+// Block loads (each block entry is read once per pass): plain non-coherent loads.  The
+// evict-first hint (ld.global.cs) was measured slower on every stencil and half apply at 16^4,
+// n = 48 (FP32 S apply 1883-2366 us vs 1594-1614 us, BF16 904-916 vs 833-852, full FP32
+// stencil 1152 vs 969), the more so after any other kernel had touched memory, while DRAM
+// traffic stayed at the algorithmic bytes either way.
+template <class T> __device__ __forceinline__ T ld_stream(const T* p) { return __ldg(p); }
 
 template <class AC, class BT> struct LoadS;
 template <> struct LoadS<double2, double2> {
