@@ -727,7 +727,7 @@ def run_schur_only(args):
 
 def run_mrhs(args):
     """Multi-right-hand-side BF16 apply on tensor cores vs one single-column BF16 apply per column:
-    coarse 4^4 / 6^4 / 8^4 (V = 256, 1296, 4096), n = 16 / 32 / 48, 1-12 columns; L2 flushed
+    coarse 4^4 / 6^4 / 8^4 (V = 256, 1296, 4096), n = 16 / 32 / 48, 1-16 columns; L2 flushed
     (256 MB write) before every timed launch."""
     import torch
 
@@ -752,14 +752,14 @@ def run_mrhs(args):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    cases = [(L, nv, (1, 2, 4, 8, 12)) for L in (4, 6, 8) for nv in (8, 16, 24)]
+    cases = [(L, nv, (1, 2, 4, 8, 12, 16)) for L in (4, 6, 8) for nv in (8, 16, 24)]
     if args.mrhs_case:
         L, nv, nr = (int(v) for v in args.mrhs_case.split(","))
         cases = [(L, nv, (nr,))]
     for L, nv, counts in cases:
         op = build_coarse_operator((6, L, nv), (2 * L,) * 4, nv, -0.42, CSW, device=dev)
         cop = cg.CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, precisions=(cg.PREC_BF16,),
-                          max_nrhs=12)
+                          max_nrhs=16)
         del op
         torch.cuda.empty_cache()
         n, V = 2 * nv, cop.V

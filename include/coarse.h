@@ -102,10 +102,11 @@ void coarse_op_destroy(coarse_op* op);
  * x, y : device, [nrhs][V][n], complex128 for COARSE_PREC_FP64 and complex64
  *        otherwise; x and y must not overlap.
  * nrhs : 1 .. desc.max_nrhs.  nrhs > 1 with COARSE_PREC_BF16 runs a
- *        tensor-core multi-right-hand-side kernel on passes of up to 12 columns
- *        (the columns rounded to BF16, FP32 accumulation): mma.sync, or for
- *        n = 32 and 48 tcgen05.mma with tensor-memory accumulators, whichever
- *        the autotuner timed faster for the shape.  An operator created with
+ *        tensor-core multi-right-hand-side kernel (the columns rounded to BF16,
+ *        FP32 accumulation): for n = 16 mma.sync on passes of up to 12 columns;
+ *        for n = 32 and 48 passes of up to 16 columns, each run by mma.sync (up
+ *        to 12 columns) or tcgen05.mma with tensor-memory accumulators,
+ *        whichever the autotuner timed faster for the shape.  An operator created with
  *        BF16 blocks and max_nrhs > 1 keeps two more BF16 copies of its blocks
  *        (one per kernel's operand layout).
  * Asynchronous on `stream`.  The requested precision must have been enabled

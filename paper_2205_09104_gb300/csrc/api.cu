@@ -334,10 +334,12 @@ int coarse_op_create(const coarse_op_desc* d, const void* self_blocks, const voi
   if ((op->precisions & (1u << COARSE_PREC_BF16)) && op->max_nrhs > 1) {
     op->mrhs.bytes = nblk * sizeof(cbf16);
     CREATE_TRY(dmalloc((char**)&op->mrhs.ptr, op->mrhs.bytes));
-    // 12 columns as mma.sync fragments, or as the two tcgen05 B-operand variants (twice that)
-    op->mrhs_x.bytes = 24 * N * sizeof(cbf16);
+    // 12 columns as mma.sync fragments (12 N BF16 pairs); where the tcgen05 kernel exists,
+    // also 16 columns as its two B-operand variants (32 N)
+    const bool tc = op->n == 32 || op->n == 48;
+    op->mrhs_x.bytes = (tc ? 32 : 12) * N * sizeof(cbf16);
     CREATE_TRY(dmalloc((char**)&op->mrhs_x.ptr, op->mrhs_x.bytes));
-    if (op->n == 32 || op->n == 48) {
+    if (tc) {
       op->umma.bytes = nblk * sizeof(cbf16);
       CREATE_TRY(dmalloc((char**)&op->umma.ptr, op->umma.bytes));
     }

@@ -165,6 +165,11 @@ int launch_mrhs_cfg(MrhsArgs a, int S, cudaStream_t s) {
 template <int N, int T>
 std::vector<TuneChoice> mrhs_candidates(bool tc) {
   std::vector<TuneChoice> c;
+  if constexpr (T > kMrhsMaxT) {  // 16-column passes: the tcgen05 kernel only
+    if (tc && (N == 32 || N == 48))
+      for (int k = 1; k <= 2; ++k) c.push_back({100 + k, 0, 0});
+    return c;
+  }
   const int def_p = N == 16 ? 4 : (N == 32 ? 2 : 1);
   const int ps[3] = {N == 16 ? 2 : 1, N == 16 ? 4 : 2, N == 16 ? 8 : 4};
   c.push_back({def_p, 0, 0});
@@ -195,11 +200,17 @@ int launch_mrhs_frag(const MrhsArgs& a, int S, cudaStream_t s) {
 template <int N, int T>
 int launch_mrhs_choice(const MrhsArgs& a, const TuneChoice& c, cudaStream_t s) {
   switch (c.a) {
-    case 1: return launch_mrhs_frag<N, T, 1>(a, c.b, s);
-    case 2: return launch_mrhs_frag<N, T, 2>(a, c.b, s);
-    case 4: return launch_mrhs_frag<N, T, 4>(a, c.b, s);
+    case 1:
+      if constexpr (T <= kMrhsMaxT) return launch_mrhs_frag<N, T, 1>(a, c.b, s);
+      break;
+    case 2:
+      if constexpr (T <= kMrhsMaxT) return launch_mrhs_frag<N, T, 2>(a, c.b, s);
+      break;
+    case 4:
+      if constexpr (T <= kMrhsMaxT) return launch_mrhs_frag<N, T, 4>(a, c.b, s);
+      break;
     case 8:
-      if constexpr (N == 16) return launch_mrhs_frag<N, T, 8>(a, c.b, s);
+      if constexpr (N == 16 && T <= kMrhsMaxT) return launch_mrhs_frag<N, T, 8>(a, c.b, s);
       break;
     case 101:
     case 102:
@@ -244,6 +255,10 @@ int launch_mrhs_n(const MrhsArgs& a, cudaStream_t s) {
     case 1: return launch_mrhs_t<N, 1>(a, s);
     case 2: return launch_mrhs_t<N, 2>(a, s);
     case 3: return launch_mrhs_t<N, 3>(a, s);
+    case 4:
+      if constexpr (N == 32 || N == 48)
+        if (a.tcblk) return launch_mrhs_t<N, 4>(a, s);
+      break;
   }
   set_error("multi-RHS apply: %d columns in one pass", a.R);
   return COARSE_ERR_INVALID_ARG;
@@ -277,7 +292,9 @@ int launch_apply_mrhs_bf16(const coarse_op* op, const void* x, void* y, int nrhs
     return COARSE_ERR_INVALID_ARG;
   }
   const long long col = (long long)op->V * op->n;
-  for (int c0 = 0; c0 < nrhs; c0 += kMrhsPass) {
+  // passes of 16 columns where the tcgen05 kernel exists (its accumulators hold 16), else 12
+  const int pass = op->umma.ptr ? kTcPass : kMrhsPass;
+  for (int c0 = 0; c0 < nrhs; c0 += pass) {
     MrhsArgs a{};
     a.frag = (const uint4*)op->mrhs.ptr;
     a.nb = op->nb;
@@ -285,7 +302,7 @@ int launch_apply_mrhs_bf16(const coarse_op* op, const void* x, void* y, int nrhs
     a.xb = (const uint2*)op->mrhs_x.ptr;
     a.y = (float2*)y + c0 * col;
     a.ldx = a.ldy = col;
-    a.R = nrhs - c0 < kMrhsPass ? nrhs - c0 : kMrhsPass;
+    a.R = nrhs - c0 < pass ? nrhs - c0 : pass;
     a.tcblk = op->umma.ptr;
     a.V = op->V;
     a.mu = (float)(adjoint ? -op->mu : op->mu);

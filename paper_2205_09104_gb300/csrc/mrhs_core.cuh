@@ -29,6 +29,7 @@ constexpr int kMrhsTile = 4;    // columns per tensor-core tile (B operand is 8 
 constexpr int kMrhsMaxT = 3;    // tiles per pass: up to 12 columns
 constexpr int kMrhsPass = kMrhsTile * kMrhsMaxT;
 constexpr int kMrhsColumns = kMrhsPass;  // columns one pass (and one batched operator) can carry
+constexpr int kTcPass = 16;              // columns of one pass of the tcgen05 kernel (4 tiles)
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint4& a, uint32_t b0, uint32_t b1) {
   asm volatile(

@@ -66,7 +66,7 @@ __host__ __device__ constexpr int tc_split(int S) {
 }
 
 // Tensor-memory columns: 2 accumulator sets x 4 accumulators of width N = 8T, in slots of 16
-// columns (T <= 2: 128 columns per CTA, up to 3 CTAs per SM) or 32 (T = 3: 256, up to 2).
+// columns (T <= 2: 128 columns per CTA, up to 3 CTAs per SM) or 32 (T = 3, 4: 256, up to 2).
 __host__ __device__ constexpr uint32_t tc_slot(int T) { return T <= 2 ? 16u : 32u; }
 __host__ __device__ constexpr uint32_t tc_cols(int T) { return 8u * tc_slot(T); }
 
@@ -414,6 +414,8 @@ int launch_apply_mrhs_tc(TcArgs a, int T, int ctas_per_sm, int S, cudaStream_t s
     case 48 * 8 + 1: return launch_tc_nt<48, 1>(a, ctas_per_sm, S, s);
     case 48 * 8 + 2: return launch_tc_nt<48, 2>(a, ctas_per_sm, S, s);
     case 48 * 8 + 3: return launch_tc_nt<48, 3>(a, ctas_per_sm, S, s);
+    case 32 * 8 + 4: return launch_tc_nt<32, 4>(a, ctas_per_sm, S, s);
+    case 48 * 8 + 4: return launch_tc_nt<48, 4>(a, ctas_per_sm, S, s);
   }
   set_error("tcgen05 multi-RHS apply: unsupported n = %d with %d column tiles", a.n, T);
   return COARSE_ERR_INVALID_ARG;

@@ -1,7 +1,8 @@
 """GPU parity of the tcgen05 multi-right-hand-side apply (csrc/mrhs_tc.cu: BF16 operands read by
 the tensor core from shared memory, FP32 accumulators in tensor memory) for n = 32 and 48, with
 each launch configuration the autotuner may pick fixed in turn through coarse_autotune_set:
-one to three CTAs per SM, all stages that fit or a 2- / 3-stage ring.
+one to three CTAs per SM, all stages that fit or a 2- / 3-stage ring, and passes of 1 to 16
+columns (13-16 columns: one pass of four column tiles, which only this kernel runs).
 
 The bar is the one of the mma.sync kernel: against the oracle applied in FP64 to the BF16-rounded
 forward blocks (backward hops rebuilt from them by sigma3 F^H sigma3) and the BF16-rounded
@@ -27,13 +28,13 @@ from oracle.lattice import neighbours
 pytestmark = pytest.mark.gpu
 
 # (100 + CTAs per SM, stages (0: all that fit)); 3 CTAs per SM exist only for passes of up to 8
-# columns (their tensor memory), so 12-column passes run that one with 2
+# columns (their tensor memory), so passes of 9-16 columns run that one with 2
 CONFIGS = [(101, 0), (102, 0), (101, 2), (102, 3), (103, 0), (103, 2)]
 
 
 def _keys(n, V):
     vb = V.bit_length() - 1
-    return [(t, f"mrhs/n{n}/t{t}/v{vb}") for t in (1, 2, 3)]
+    return [(t, f"mrhs/n{n}/t{t}/v{vb}") for t in (1, 2, 3, 4)]
 
 
 def _fix(n, V, cfg):
@@ -66,7 +67,7 @@ def small():
 
 @pytest.mark.parametrize("nv", [16, 24])
 @pytest.mark.parametrize("cfg", CONFIGS)
-@pytest.mark.parametrize("nrhs", [2, 7, 12, 13])
+@pytest.mark.parametrize("nrhs", [2, 7, 12, 13, 16, 19])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_tc_small_lattices(small, nv, cfg, nrhs, adjoint):
     from paper_2205_09104_gb300 import CoarseOp
@@ -112,10 +113,10 @@ def test_tc_many_sites_per_cta(coarse8, nv, cfg):
     sites = np.unique(np.concatenate([[0, V - 1], rng.integers(0, V, 30)]))
     rb = bf16_blocks_of(site_blocks(op, sites), op.dims)
     s3 = ocoarse.sigma3(n // 2)
-    dev = CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, mu=mu, precisions=(2,), max_nrhs=12)
+    dev = CoarseOp(op.self_blocks, op.hop_blocks, op.dims, op.nv, mu=mu, precisions=(2,), max_nrhs=16)
     _fix(n, V, cfg)
     try:
-        for nrhs, adjoint in ((12, False), (12, True), (5, False), (8, True)):
+        for nrhs, adjoint in ((12, False), (12, True), (5, False), (8, True), (16, False), (14, True)):
             Xd = torch.from_numpy(rhs((531, nv, nrhs), nrhs, V * n)).to("cuda", torch.complex64)
             Y = dev.apply(Xd, precision=2, adjoint=adjoint).cpu().numpy().astype(np.complex128)
             X32 = Xd.cpu().numpy().astype(np.complex128)
